@@ -1,0 +1,185 @@
+"""CPU oracle for the Euler characteristic curve -- TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU legs of ``bench.py``
+(``cpu_baseline`` and ``--impl reference``) may import this package.  The
+product library never imports it, and it imports nothing from the product.
+
+The arithmetic lives in ``ecc_oracle.c`` (plain single-threaded C, one cell at
+a time, following Sec. 2.1-2.3 of Wang, Wagner, Chen, SoCG 2022).  This module
+only compiles it with gcc, marshals numpy arrays, and -- for full-size checks
+-- runs the oracle's own slab entry points (the chunking of Sec. 3.4) on
+several host threads and sums their histograms.
+
+Parity status: every function here is pinned by the ``-m "not gpu"`` tests in
+``tests/test_oracle_pins.py`` (brute force on tiny inputs, Betti numbers by
+flood fill, closed forms, symmetries, and a mutation check).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+from pathlib import Path
+
+import numpy as np
+
+_HERE = Path(__file__).resolve().parent
+_SRC = _HERE / "ecc_oracle.c"
+_BUILD = _HERE / "_build"
+_LIB_PATH = _BUILD / "libecc_oracle.so"
+
+VERTEX = "vertex"    # cells enter at the max of their vertices (pixels as vertices)
+TOPCELL = "topcell"  # voxels are top cells; lower cells take the min of their cofaces (Sec. 2.1)
+
+_lib = None
+_lock = threading.Lock()
+
+
+def build(src: Path = _SRC, out: Path = _LIB_PATH, extra_flags=()) -> Path:
+    """Compile the oracle with gcc into a shared library; returns its path."""
+    out.parent.mkdir(parents=True, exist_ok=True)
+    cmd = ["gcc", "-O2", "-std=c11", "-shared", "-fPIC", *extra_flags, str(src), "-o", str(out)]
+    subprocess.run(cmd, check=True)
+    return out
+
+
+def load(path: Path | None = None):
+    """Load (building if needed) the oracle library and declare its signatures."""
+    global _lib
+    if path is None:
+        with _lock:
+            if _lib is not None:
+                return _lib
+            if not _LIB_PATH.exists() or _LIB_PATH.stat().st_mtime < _SRC.stat().st_mtime:
+                build()
+            _lib = _declare(ctypes.CDLL(str(_LIB_PATH)))
+            return _lib
+    return _declare(ctypes.CDLL(str(path)))
+
+
+def _declare(lib):
+    i64p = ctypes.POINTER(ctypes.c_int64)
+    for name in ("oracle_vcec_vertex_rows", "oracle_vcec_topcell_rows"):
+        f = getattr(lib, name)
+        f.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, i64p,
+                      ctypes.c_int64, ctypes.c_int64, ctypes.c_int32, ctypes.c_int32, i64p]
+        f.restype = ctypes.c_int
+    for name in ("oracle_vcec_vertex", "oracle_vcec_topcell"):
+        f = getattr(lib, name)
+        f.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, i64p,
+                      ctypes.c_int32, ctypes.c_int32, i64p]
+        f.restype = ctypes.c_int
+    lib.oracle_ecc_from_vcec.argtypes = [i64p, ctypes.c_int64, i64p]
+    lib.oracle_ecc_from_vcec.restype = None
+    return lib
+
+
+def _dtype_code(a: np.ndarray) -> int:
+    if a.dtype == np.uint8:
+        return 1
+    if a.dtype == np.uint16:
+        return 2
+    raise TypeError(f"oracle supports uint8/uint16 images, got {a.dtype}")
+
+
+def _i64p(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int64))
+
+
+class OracleError(RuntimeError):
+    pass
+
+
+def _check(rc: int):
+    if rc == 1:
+        raise OracleError("invalid arguments")
+    if rc == 2:
+        raise OracleError("image value outside [lo, hi]")
+
+
+def _default_range(img: np.ndarray, lo, hi):
+    if lo is None:
+        lo = 0
+    if hi is None:
+        hi = 255 if img.dtype == np.uint8 else 65535
+    return int(lo), int(hi)
+
+
+def vcec(img: np.ndarray, lo=None, hi=None, mode: str = VERTEX, lib=None) -> np.ndarray:
+    """VCEC (int64[hi-lo+1]) of a dense uint8/uint16 image, single-threaded."""
+    lib = lib or load()
+    img = np.ascontiguousarray(img)
+    lo, hi = _default_range(img, lo, hi)
+    dims = np.asarray(img.shape, dtype=np.int64)
+    out = np.zeros(hi - lo + 1, dtype=np.int64)
+    fn = lib.oracle_vcec_vertex if mode == VERTEX else lib.oracle_vcec_topcell
+    _check(fn(img.ctypes.data, _dtype_code(img), img.ndim, _i64p(dims), lo, hi, _i64p(out)))
+    return out
+
+
+def ecc_from_vcec(v: np.ndarray, lib=None) -> np.ndarray:
+    lib = lib or load()
+    v = np.ascontiguousarray(v, dtype=np.int64)
+    out = np.empty_like(v)
+    lib.oracle_ecc_from_vcec(_i64p(v), v.size, _i64p(out))
+    return out
+
+
+def ecc(img: np.ndarray, lo=None, hi=None, mode: str = VERTEX, lib=None) -> np.ndarray:
+    """ECC (int64[hi-lo+1]): ECC[g] = chi(K_{<= lo+g})."""
+    lib = lib or load()
+    return ecc_from_vcec(vcec(img, lo, hi, mode, lib), lib)
+
+
+def vcec_rows(img: np.ndarray, begin: int, end: int, lo=None, hi=None, mode: str = VERTEX,
+              lib=None) -> np.ndarray:
+    """VCEC of the cells whose dims[0] index lies in [begin, end).
+
+    V-mode indexes base points 0..dims[0]-1; T-mode indexes elementary
+    intervals 0..2*dims[0] (even = degenerate).  Disjoint ranges add up.
+    """
+    lib = lib or load()
+    img = np.ascontiguousarray(img)
+    lo, hi = _default_range(img, lo, hi)
+    dims = np.asarray(img.shape, dtype=np.int64)
+    out = np.zeros(hi - lo + 1, dtype=np.int64)
+    fn = lib.oracle_vcec_vertex_rows if mode == VERTEX else lib.oracle_vcec_topcell_rows
+    _check(fn(img.ctypes.data, _dtype_code(img), img.ndim, _i64p(dims), int(begin), int(end),
+              lo, hi, _i64p(out)))
+    return out
+
+
+def row_extent(img_shape, mode: str = VERTEX) -> int:
+    """Number of dims[0] indices the *_rows entry points range over."""
+    return img_shape[0] if mode == VERTEX else 2 * img_shape[0] + 1
+
+
+def vcec_parallel(img: np.ndarray, lo=None, hi=None, mode: str = VERTEX, threads: int | None = None,
+                  rows: tuple[int, int] | None = None) -> np.ndarray:
+    """Run the single-threaded oracle on disjoint dims[0] slabs in host threads
+    (ctypes releases the GIL) and sum the slab histograms.  ``rows`` restricts
+    the work to a sub-range of the dims[0] indices."""
+    lib = load()
+    img = np.ascontiguousarray(img)
+    lo, hi = _default_range(img, lo, hi)
+    begin, end = rows if rows is not None else (0, row_extent(img.shape, mode))
+    threads = max(1, min(threads or os.cpu_count() or 1, end - begin))
+    cuts = np.linspace(begin, end, threads + 1).round().astype(np.int64)
+    parts = [None] * threads
+    errors = []
+
+    def work(i):
+        try:
+            parts[i] = vcec_rows(img, cuts[i], cuts[i + 1], lo, hi, mode, lib)
+        except Exception as e:  # surfaced below
+            errors.append(e)
+
+    ts = [threading.Thread(target=work, args=(i,)) for i in range(threads)]
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join()
+    if errors:
+        raise errors[0]
+    return np.sum(parts, axis=0).astype(np.int64)
