@@ -1,0 +1,318 @@
+"""Benchmark: exact ECC of a 512^3 uint8 Gaussian-smoothed volume on GB300.
+
+One step = the whole per-image hot path through the C ABI (``ecc_compute``):
+stencil + histogram kernel, then the device scan.  The input is resident in
+HBM; L2 is flushed (a 2x-L2 write) before every timed step and each step is
+timed with CUDA events on the launching stream.
+
+Also reported on the same JSON line:
+  roofline      the stencil kernel's algorithmic bytes per launch
+                (voxels x bytes/voxel + nbins x 8) over its event-timed
+                duration, against the measured HBM copy bandwidth;
+  e2e           the same metric through ``ecc_compute_host`` from pinned host
+                memory (chunked H2D overlapped with the kernels, ECC copied
+                back), copies inside the timed region;
+  cpu_baseline  the CPU oracle (as it stands) on a bounded slab of the same
+                volume, on all host cores;
+  batched, serving  optional (--extras): the uneven-batch and serving
+                workloads, summarized.
+
+``--impl reference`` times the CPU oracle on the same workload (bounded slab
+samples per step) and prints the same line with "impl": "reference".
+
+Multi-GPU (torchrun, N ranks): replicas only -- every rank runs the same
+independent workload on its own GPU; no data-path collective; value is the
+voxels of all ranks over the max time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+from pathlib import Path
+
+ROOT = Path(__file__).resolve().parent
+sys.path.insert(0, str(ROOT))
+
+METRIC = "ECC Gvoxel/s"
+UNIT = "Gvoxel/s"
+WORKLOAD = "plain 3D ECC, 512x512x512 uint8 Gaussian-smoothed (sigma=4) field, seed 1, 256 bins, vertex complex"
+
+
+def _peaks():
+    p = ROOT / "MEASURED_PEAKS.json"
+    if p.exists():
+        d = json.loads(p.read_text())
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def _traffic_for(kernel_digest: str):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel is unchanged."""
+    p = ROOT / "profiles" / "traffic.json"
+    if not p.exists():
+        return None
+    d = json.loads(p.read_text())
+    ent = d.get("stencil_512cube_u8")
+    if not ent or ent.get("kernel_digest") != kernel_digest:
+        return None
+    return ent.get("dram_bytes_per_launch")
+
+
+def _kernel_digest():
+    import hashlib
+    h = hashlib.sha256()
+    for p in sorted((ROOT / "paper_2203_09087_gb300" / "csrc").glob("*")):
+        h.update(p.read_bytes())
+    return h.hexdigest()[:16]
+
+
+class ClockSampler:
+    def __init__(self, path):
+        self.path = path
+        self.proc = None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            dev = os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")[0] or str(os.environ.get("LOCAL_RANK", 0))
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={dev}", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        for line in Path(self.path).read_text().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws > 1:
+        import torch.distributed as dist
+        if not dist.is_initialized():
+            dist.init_process_group("nccl")
+        return dist, dist.get_rank(), ws
+    return None, 0, 1
+
+
+def _barrier(dist, torch):
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+
+
+def _max_over_ranks(dist, torch, x: float) -> float:
+    if not dist:
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def cpu_oracle_sample(vol_host, budget_s: float = 12.0, threads: int | None = None):
+    """Time the oracle (all host cores) on a slab of planes sized for ~budget_s of CPU time."""
+    import numpy as np
+
+    import oracle
+    threads = threads or os.cpu_count() or 1
+    # calibrate on one plane with one thread
+    t0 = time.perf_counter()
+    oracle.vcec_rows(vol_host, 0, 1, 0, 255, oracle.VERTEX)
+    per_plane = max(time.perf_counter() - t0, 1e-4)
+    planes = int(max(threads, min(vol_host.shape[0], budget_s / per_plane)))
+    planes = min(planes, vol_host.shape[0])
+    t0 = time.perf_counter()
+    oracle.vcec_parallel(vol_host, 0, 255, oracle.VERTEX, threads=threads, rows=(0, planes))
+    dt = time.perf_counter() - t0
+    vox = planes * vol_host.shape[1] * vol_host.shape[2]
+    return {"value": vox / dt / 1e9, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"cells based on planes 0..{planes - 1} of the same volume ({vox} voxels), "
+                      f"slab-parallel over {threads} threads, {dt:.2f} s wall"}
+
+
+def run_reference(args):
+    """The CPU oracle as the reference arm (rank 0 only)."""
+    import torch
+    dist, rank, ws = None, int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1"))
+    if rank != 0:
+        return 0
+    import synth
+    dev = "cuda" if torch.cuda.is_available() else "cpu"
+    vol = synth.config2_smooth_3d(device=dev).cpu().numpy()
+    import oracle
+    threads = os.cpu_count() or 1
+    # each step: the oracle on a bounded slab (about 10 s of CPU work)
+    t0 = time.perf_counter()
+    oracle.vcec_rows(vol, 0, 1, 0, 255, oracle.VERTEX)
+    per_plane = max(time.perf_counter() - t0, 1e-4)
+    planes = int(max(threads, min(vol.shape[0], 10.0 / per_plane)))
+    rows = (0, min(planes, vol.shape[0]))
+    for _ in range(args.warmup):
+        oracle.vcec_parallel(vol[: rows[1] + 1], 0, 255, oracle.VERTEX, threads=threads, rows=rows)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        oracle.vcec_parallel(vol[: rows[1] + 1], 0, 255, oracle.VERTEX, threads=threads, rows=rows)
+    dt = time.perf_counter() - t0
+    vox = (rows[1] - rows[0]) * vol.shape[1] * vol.shape[2]
+    value = vox * args.steps / dt / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "sample_planes": rows[1] - rows[0]},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": f"cells based on planes {rows[0]}..{rows[1] - 1} per step"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--kernel", default="default", choices=["default", "direct"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
+    ap.add_argument("--extras", action="store_true", help="also run the batched and serving workloads")
+    ap.add_argument("--shape", default="512,512,512")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+
+    import paper_2203_09087_gb300 as ecc
+    import synth
+
+    dist, rank, ws = _dist()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    shape = tuple(int(x) for x in args.shape.split(","))
+    vol = synth.config2_smooth_3d(device="cuda", shape=shape)
+    nvox = vol.numel()
+    flags = ecc.ECC_FLAG_TIME_KERNELS | (ecc.ECC_FLAG_KERNEL_DIRECT if args.kernel == "direct" else 0)
+    plan = ecc.ecc_plan("u8", 0, 255, max_voxels=nvox, flags=flags)
+    out = torch.empty(256, dtype=torch.int64, device="cuda")
+    l2 = torch.cuda.get_device_properties(local).L2_cache_size
+    flush = torch.empty(2 * l2 + (1 << 20), dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    os.makedirs(ROOT / "gpurun_out", exist_ok=True)
+
+    # correctness guard on the benchmarked volume: last ECC value of a full box is 1
+    ecc.ecc_compute(plan, vol, out)
+    ecc.ecc_status_get(plan)
+    assert int(out[-1].item()) == 1
+    ecc.ecc_plan_kernel_time(plan)
+
+    sampler = ClockSampler(str(ROOT / "gpurun_out" / f"clocks_rank{rank}.csv"))
+    with sampler:
+        # warm-up (at least W steps and about a second, so clocks are sampled under load)
+        t_end = time.perf_counter() + 1.0
+        w = 0
+        while w < args.warmup or time.perf_counter() < t_end:
+            flush.fill_(w & 0xFF)
+            ecc.ecc_compute(plan, vol, out)
+            w += 1
+        ecc.ecc_plan_kernel_time(plan)
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        _barrier(dist, torch)
+        for i in range(args.steps):
+            flush.fill_(i & 0xFF)
+            starts[i].record(stream)
+            ecc.ecc_compute(plan, vol, out)
+            ends[i].record(stream)
+        _barrier(dist, torch)
+        launches_per_step = ecc.ecc_plan_last_launches(plan)
+        step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+        kern_ms, kern_n = ecc.ecc_plan_kernel_time(plan)
+
+        # end to end from pinned host memory through ecc_compute_host
+        host = vol.cpu().pin_memory().numpy()
+        e2e_out = np.empty(256, np.int64)
+        for _ in range(3):
+            ecc.ecc_compute_host(plan, host, e2e_out)
+        ecc.ecc_plan_kernel_time(plan)
+        e2e_steps = max(3, min(args.steps, 20))
+        _barrier(dist, torch)
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            ecc.ecc_compute_host(plan, host, e2e_out)
+        _barrier(dist, torch)
+        e2e_s = time.perf_counter() - t0
+        ecc.ecc_plan_kernel_time(plan)
+        assert np.array_equal(e2e_out, out.cpu().numpy())
+
+    total_ms = _max_over_ranks(dist, torch, sum(step_ms))
+    e2e_s = _max_over_ranks(dist, torch, e2e_s)
+    value = nvox * args.steps * ws / (total_ms * 1e-3) / 1e9
+    e2e_value = nvox * e2e_steps * ws / e2e_s / 1e9
+
+    peak, peak_src = _peaks()
+    alg_bytes = nvox * 1 + 256 * 8
+    kern_avg_s = kern_ms / max(kern_n, 1) * 1e-3
+    achieved = alg_bytes / kern_avg_s / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                "traffic": _traffic_for(_kernel_digest()), "peak_source": peak_src,
+                "kernel_us": kern_avg_s * 1e6, "algorithmic_bytes_per_launch": alg_bytes}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "shape": list(shape), "nbins": 256, "complex": "vertex",
+                       "parallelism": f"replicas{ws}", "l2": "flushed (2x L2 write) before every step",
+                       "kernel": args.kernel},
+            "roofline": roofline,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": nvox, "d2h_bytes_per_step": 256 * 8,
+                    "path": "ecc_compute_host, pinned host input, chunked H2D overlapped with kernels"},
+            "gpu_launches": launches_per_step * args.steps,
+            "clocks": sampler.summary()}
+    if rank == 0 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_oracle_sample(vol.cpu().numpy())
+    if args.extras and rank == 0:
+        from bench_extras import run_batched, run_serving  # noqa
+        line["batched"] = run_batched()
+        line["serving"] = run_serving()
+    if rank == 0:
+        print(json.dumps(line))
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

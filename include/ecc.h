@@ -1,0 +1,234 @@
+/*
+ * ecc.h -- C ABI of the GB300 (sm_103a) Euler characteristic curve library.
+ *
+ * Problem (Wang, Wagner, Chen, "GPU Computation of the Euler Characteristic
+ * Curve for Imaging Data", SoCG 2022, Sec. 2): given a 2D or 3D integer
+ * grayscale image and a gray-level range [lo, hi], return the integer vector
+ *
+ *     ECC[g] = chi(K_{<= lo+g}) = sum_j (-1)^j c_j(K_{<= lo+g}),  g = 0..hi-lo
+ *
+ * (Sec. 2.2, Eq. 1), computed as the prefix sum (Sec. 2.3) of the vector of
+ * changes VCEC, where each voxel adds (-1)^dim for every cell it introduces
+ * (Sec. 2.3 "Faces introduced by a voxel", Algorithm 1).  The paper indexes
+ * the ECC by the values present in the image (t_i in Eq. 1); this library
+ * returns every level in [lo, hi], of which the paper's sequence is the
+ * subsequence at present values.
+ *
+ * Two cubical complexes are supported (ecc_complex):
+ *   ECC_VERTEX_MAX   voxels are the VERTICES of the cubical grid; a cell
+ *                    (vertex, edge, square, cube) exists when all its vertices
+ *                    are in the image and enters at the MAX of its vertex
+ *                    values.  Each voxel introduces the cells it is the
+ *                    maximum of, ties going to the lowest linear index.
+ *   ECC_TOPCELL_MIN  voxels are the TOP-dimensional cells (Sec. 2.1); every
+ *                    lower cell takes the MIN over its top-dimensional
+ *                    cofaces, ties going to the lowest linear index
+ *                    (Sec. 2.3); the image boundary behaves like the paper's
+ *                    +infinity collar (Sec. 3.3 "Branching").
+ *
+ * Conventions (all entry points):
+ *  - Every call returns an ecc_status; no C++ exception crosses this ABI.
+ *    On failure ecc_last_error() returns a message for the calling thread.
+ *  - Image and ECC buffers passed to ecc_compute / ecc_compute_batch are
+ *    DEVICE pointers owned by the caller, who keeps them alive until the
+ *    work queued on `stream` has finished.  `stream` is a cudaStream_t
+ *    passed as void* (NULL = the legacy default stream).
+ *  - Layout: row-major, dims[0] slowest (the paper's chunking cuts along
+ *    dims[0], Sec. 3.4).  Pitches are in bytes; 0 means dense.
+ *  - Results are exact int64; there is no floating point anywhere.
+ *  - Values outside [lo, hi] are reported on the device (ECC_E_RANGE from
+ *    ecc_status_get) unless ECC_FLAG_NO_RANGE_CHECK is set; the offending
+ *    voxels contribute nothing.
+ *  - A plan is used by one host thread at a time and by one stream at a
+ *    time (calls on a plan are ordered on the stream they are issued to).
+ *    The server (ecc_server_*) is thread-safe.
+ *  - Everything runs on the CUDA device that is current when the plan or
+ *    server is created.
+ */
+#ifndef ECC_GB300_ECC_H
+#define ECC_GB300_ECC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    ECC_OK = 0,
+    ECC_E_INVALID = 1,    /* bad argument: ndim, dims, pitch, range, dtype, null pointer */
+    ECC_E_RANGE = 2,      /* the device saw an image value outside [lo, hi] */
+    ECC_E_NOMEM = 3,      /* device or pinned-host allocation failed, or over the HBM budget */
+    ECC_E_CUDA = 4,       /* a CUDA runtime call failed (message in ecc_last_error) */
+    ECC_E_TIMEOUT = 5,    /* a bounded device wait or a host wait ran out */
+    ECC_E_BUSY = 6,       /* the object is in use (e.g. a batch larger than the plan) */
+    ECC_E_SHUTDOWN = 7,   /* the server is shutting down */
+    ECC_E_CANCELLED = 8   /* the job was cancelled before it ran */
+} ecc_status;
+
+typedef enum { ECC_U8 = 1, ECC_U16 = 2 } ecc_dtype;
+
+typedef enum { ECC_VERTEX_MAX = 0, ECC_TOPCELL_MIN = 1 } ecc_complex;
+
+/* One image or volume.  data: device pointer (host pointer only where an
+ * entry point says so).  ndim: 2 or 3.  dims[0..ndim-1] >= 1, dims[0]
+ * slowest.  row_pitch: bytes between consecutive rows (steps of
+ * dims[ndim-2]); slice_pitch: bytes between consecutive slices (3D only,
+ * steps of dims[0]).  0 = dense.  Pitches must be multiples of the element
+ * size and at least the dense extent. */
+typedef struct ecc_image {
+    const void *data;
+    int32_t ndim;
+    int32_t dtype;          /* ecc_dtype */
+    int64_t dims[3];
+    int64_t row_pitch;
+    int64_t slice_pitch;
+} ecc_image;
+
+/* Plan flags. */
+#define ECC_FLAG_NO_RANGE_CHECK   0x1u  /* caller guarantees lo <= value <= hi */
+#define ECC_FLAG_NO_AUTOTUNE      0x2u  /* use built-in tile defaults, never time candidates */
+#define ECC_FLAG_KERNEL_DIRECT    0x10u /* force the one-thread-per-voxel stencil kernel */
+#define ECC_FLAG_KERNEL_BITSLICE  0x20u /* force the bit-sliced stencil kernel (where it applies) */
+#define ECC_FLAG_BATCH_PER_IMAGE  0x40u /* ecc_compute_batch: one stencil launch per image (baseline) */
+#define ECC_FLAG_TIME_KERNELS     0x80u /* record CUDA events around every stencil launch */
+
+typedef struct ecc_plan_desc {
+    int32_t dtype;          /* ecc_dtype of every image computed with this plan */
+    int32_t lo, hi;         /* gray-level range; nbins = hi - lo + 1, 1 <= nbins <= 65536 */
+    int32_t complex_mode;   /* ecc_complex */
+    int32_t max_images;     /* largest batch (ecc_compute_batch); >= 1 */
+    int32_t reserved;       /* must be 0 */
+    int64_t max_voxels;     /* largest total voxel count of one call (sum over a batch) */
+    uint32_t flags;         /* ECC_FLAG_* */
+    uint32_t reserved2;     /* must be 0 */
+} ecc_plan_desc;
+
+typedef struct ecc_plan_s *ecc_plan_t;
+
+/* Create a plan: validates the description, picks the kernel variant and its
+ * tile shape (autotuned on first use per GPU model unless
+ * ECC_FLAG_NO_AUTOTUNE), and allocates the plan's device workspace (the
+ * int64 VCEC accumulators, scan flags and a status word) and its pinned
+ * staging buffers.  Ownership: the caller owns *out and frees it with
+ * ecc_plan_destroy.  Errors: ECC_E_INVALID, ECC_E_NOMEM, ECC_E_CUDA. */
+ecc_status ecc_plan(ecc_plan_t *out, const ecc_plan_desc *desc);
+
+/* Synchronizes the plan's pending work and frees the plan. */
+ecc_status ecc_plan_destroy(ecc_plan_t plan);
+
+/* Number of bins (hi - lo + 1) of a plan, or -1 for an invalid handle. */
+int32_t ecc_plan_nbins(ecc_plan_t plan);
+
+/* ECC of one image, asynchronously on `stream` (Sec. 2.3: per-voxel
+ * contributions into a histogram over gray levels, then the prefix sum).
+ *   img       device image; img->dtype must equal the plan's dtype and its
+ *             voxel count must not exceed max_voxels.
+ *   d_ecc     device int64[nbins], written: ECC[g] = chi(K_{<= lo+g}).
+ *   d_vcec    optional device int64[nbins] (NULL to skip), written with the
+ *             VCEC (per-level change of the Euler characteristic).
+ * No host synchronization; device-detected errors are read with
+ * ecc_status_get.  Errors returned directly: ECC_E_INVALID, ECC_E_CUDA. */
+ecc_status ecc_compute(ecc_plan_t plan, const ecc_image *img, int64_t *d_ecc,
+                       int64_t *d_vcec, void *stream);
+
+/* Same as ecc_compute, but the image and the ECC live in HOST memory: the
+ * image is copied to the device in chunks along dims[0] on the plan's copy
+ * stream while earlier chunks are processed (the paper's streaming with a
+ * one-voxel collar and copy/compute overlap, Sec. 3.4), and the ECC is
+ * copied back.  Synchronous: returns when h_ecc is written.  Pinned host
+ * memory gives the fastest copies; pageable memory works.  Errors as
+ * ecc_compute plus ECC_E_RANGE (device errors are checked before return). */
+ecc_status ecc_compute_host(ecc_plan_t plan, const ecc_image *h_img, int64_t *h_ecc, void *stream);
+
+/* ECC of n images of arbitrary, uneven shapes in ONE persistent kernel that
+ * walks a device-side tile work list (per-image histogram offsets), launched
+ * through a CUDA graph captured once per plan, followed by one segmented
+ * scan.  Table 3 of the paper motivates batching: per-image overhead
+ * amortizes over many images.
+ *   host_descs  host array of n image descriptors (device data pointers, all
+ *               of the plan's dtype, ndim 2 or 3 mixed freely).
+ *   d_ecc       device int64[n][nbins]; row i is the ECC of image i.
+ * Asynchronous on `stream`; the descriptor array is copied before return.
+ * Errors: ECC_E_INVALID, ECC_E_BUSY (n > max_images or total voxels >
+ * max_voxels), ECC_E_CUDA. */
+ecc_status ecc_compute_batch(ecc_plan_t plan, int32_t n, const ecc_image *host_descs,
+                             int64_t *d_ecc, void *stream);
+
+/* Waits for the plan's work on `stream`, then returns and clears the device
+ * status word: ECC_OK, ECC_E_RANGE (a value outside [lo, hi] was seen) or
+ * ECC_E_TIMEOUT (a bounded device-side wait gave up). */
+ecc_status ecc_status_get(ecc_plan_t plan, void *stream);
+
+/* Number of kernels the last ecc_compute / ecc_compute_batch call enqueued
+ * (for launch accounting); -1 for an invalid handle. */
+int32_t ecc_plan_last_launches(ecc_plan_t plan);
+
+/* With ECC_FLAG_TIME_KERNELS: total device time in ms of the stencil
+ * launches recorded since the previous call (measured with CUDA events on
+ * the launching stream; the paper's "exec (kernel)" column of Table 1), and
+ * how many launches that covers.  Waits for the recorded events; resets the
+ * record.  Errors: ECC_E_INVALID (flag not set), ECC_E_CUDA. */
+ecc_status ecc_plan_kernel_time(ecc_plan_t plan, double *ms, int64_t *launches);
+
+/* Thread-local message describing the last failure of this thread. */
+const char *ecc_last_error(void);
+
+/* ------------------------------------------------------------------ serving
+ * A request loop for mixed-size, mixed-dtype ECC jobs (continuous batching).
+ * Jobs are admitted against an HBM budget (input copy + histogram +
+ * workspace); admitted jobs are packed into batched persistent launches on
+ * one of n_streams streams as slots free up, so jobs arriving while others
+ * run join the next launch.  Not in the paper; it composes the batched path
+ * above with the copy/compute overlap of Sec. 3.4.
+ */
+typedef struct ecc_server_s *ecc_server_t;
+
+typedef void (*ecc_done_fn)(uint64_t ticket, ecc_status status, void *user);
+
+typedef struct ecc_server_desc {
+    int64_t hbm_budget_bytes;  /* total device bytes the server may hold for jobs */
+    int32_t n_streams;         /* concurrent batch launches (>= 1) */
+    int32_t max_batch;         /* most jobs packed into one launch (>= 1) */
+    int64_t max_job_voxels;    /* largest single job accepted */
+    uint32_t flags;            /* ECC_FLAG_NO_RANGE_CHECK honoured */
+    uint32_t reserved;
+} ecc_server_desc;
+
+/* Creates the server and its scheduler thread on the current device. */
+ecc_status ecc_server_create(ecc_server_t *out, const ecc_server_desc *desc);
+
+/* Submits one job; thread-safe; returns immediately with *ticket_out.
+ *   img   image descriptor; data is a HOST pointer (the server copies it into
+ *         a budgeted device buffer at admission) when `host_input` is non-zero,
+ *         else a DEVICE pointer the caller keeps alive until completion.
+ *   lo, hi, complex_mode  as in ecc_plan_desc (nbins <= 65536).
+ *   out_ecc  host int64[nbins] written at completion (NULL to skip; then
+ *            read it with ecc_server_result before ecc_release).
+ *   done  optional callback run on the server's completion thread.
+ * Errors: ECC_E_INVALID, ECC_E_NOMEM (the job alone exceeds the budget),
+ * ECC_E_SHUTDOWN. */
+ecc_status ecc_submit(ecc_server_t server, const ecc_image *img, int32_t host_input,
+                      int32_t lo, int32_t hi, int32_t complex_mode, int64_t *out_ecc,
+                      ecc_done_fn done, void *user, uint64_t *ticket_out);
+
+/* Blocks until the job finishes or timeout_us elapses (< 0: no limit).
+ * Returns the job's status, or ECC_E_TIMEOUT. */
+ecc_status ecc_wait(ecc_server_t server, uint64_t ticket, int64_t timeout_us);
+
+/* Latency/throughput counters since creation (or the last reset).
+ *   out[0] jobs completed, out[1] voxels completed, out[2] p50 latency (us),
+ *   out[3] p99 latency (us), out[4] max latency (us), out[5] batch launches,
+ *   out[6] busy wall time (us), out[7] peak budget bytes in use.
+ * Latency = completion - submission.  n_out <= 8 values are written. */
+ecc_status ecc_server_stats(ecc_server_t server, double *out, int32_t n_out, int32_t reset);
+
+/* Stops accepting jobs, drains (or cancels, if cancel != 0) queued jobs,
+ * joins the threads and frees everything. */
+ecc_status ecc_server_destroy(ecc_server_t server, int32_t cancel);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ECC_GB300_ECC_H */

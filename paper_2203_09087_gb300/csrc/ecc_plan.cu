@@ -1,0 +1,83 @@
+// ecc_plan.cu -- plan workspace allocation and release.
+#include <cuda_runtime.h>
+
+#include <cstring>
+
+#include "ecc_plan.h"
+
+using namespace ecc;
+
+static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+ecc_status ecc_plan_s::allocate()
+{
+    const int64_t max_seg = d.max_images;
+    max_tiles = (int32_t)scan_tiles(max_seg, nbins);
+    const size_t acc_bytes = align_up(sizeof(unsigned long long) * (size_t)max_seg * nbins, 256);
+    const size_t status_bytes = 256;
+    const size_t counters_bytes = 256;
+    const size_t tstat_bytes = align_up(sizeof(int) * (size_t)max_tiles, 256);
+    const size_t tval_bytes = align_up(sizeof(long long) * 2 * (size_t)max_tiles, 256);
+    ws_bytes = acc_bytes + status_bytes + counters_bytes + tstat_bytes + tval_bytes;
+    cudaError_t e = cudaMalloc(&ws, ws_bytes);
+    if (e != cudaSuccess) {
+        ws = nullptr;
+        cudaGetLastError();
+        set_error("ecc_plan: cudaMalloc of the workspace failed");
+        return ECC_E_NOMEM;
+    }
+    e = cudaMemset(ws, 0, ws_bytes);
+    if (e != cudaSuccess) return cuda_fail(e, "ecc_plan: workspace clear");
+    unsigned char *b = static_cast<unsigned char *>(ws);
+    acc = reinterpret_cast<unsigned long long *>(b);
+    b += acc_bytes;
+    status = reinterpret_cast<unsigned int *>(b);
+    b += status_bytes;
+    scan_counters = reinterpret_cast<unsigned int *>(b);
+    b += counters_bytes;
+    tile_status = reinterpret_cast<int *>(b);
+    b += tstat_bytes;
+    tile_value = reinterpret_cast<long long *>(b);
+    return ECC_OK;
+}
+
+ecc_status ecc_plan_s::ensure_stage(int64_t bytes)
+{
+    if (!copy_stream) {
+        cudaError_t e = cudaStreamCreateWithFlags(&copy_stream, cudaStreamNonBlocking);
+        for (int i = 0; i < kMaxChunkEvents && e == cudaSuccess; ++i)
+            e = cudaEventCreateWithFlags(&chunk_ev[i], cudaEventDisableTiming);
+        if (e == cudaSuccess) e = cudaMalloc(&stage_ecc, sizeof(long long) * nbins);
+        if (e != cudaSuccess) return cuda_fail(e, "ecc_compute_host: stream/event setup");
+    }
+    if ((size_t)bytes > stage_bytes) {
+        if (stage) cudaFree(stage);
+        stage = nullptr;
+        stage_bytes = 0;
+        cudaError_t e = cudaMalloc(&stage, (size_t)bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            set_error("ecc_compute_host: device staging allocation failed");
+            return ECC_E_NOMEM;
+        }
+        stage_bytes = (size_t)bytes;
+    }
+    return ECC_OK;
+}
+
+void ecc_plan_s::release()
+{
+    if (batch) release_batch(this);
+    if (ws) cudaFree(ws);
+    if (stage) cudaFree(stage);
+    if (stage_ecc) cudaFree(stage_ecc);
+    for (int i = 0; i < kMaxChunkEvents; ++i)
+        if (chunk_ev[i]) cudaEventDestroy(chunk_ev[i]);
+    for (cudaEvent_t ev : time_ev) cudaEventDestroy(ev);
+    time_ev.clear();
+    if (copy_stream) cudaStreamDestroy(copy_stream);
+    ws = nullptr;
+    stage = nullptr;
+    stage_ecc = nullptr;
+    copy_stream = nullptr;
+}

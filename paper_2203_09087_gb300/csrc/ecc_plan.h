@@ -1,0 +1,71 @@
+// ecc_plan.h -- the plan object behind ecc_plan_t (internal).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <vector>
+
+#include "ecc.h"
+#include "ecc_internal.h"
+
+namespace ecc {
+
+constexpr int kMaxChunkEvents = 16;
+
+struct BatchState;  // ecc_batch.cu
+
+}  // namespace ecc
+
+struct ecc_plan_s {
+    ecc_plan_desc d{};
+    int device = 0;
+    int num_sms = 0;
+    int32_t nbins = 0;
+    int last_launches = 0;
+
+    // one device allocation: accumulators, status word, scan state
+    void *ws = nullptr;
+    size_t ws_bytes = 0;
+    unsigned long long *acc = nullptr;   // [max_images * nbins] int64, kept zero between calls
+    unsigned int *status = nullptr;      // device status word (ecc::DEV_*)
+    unsigned int *scan_counters = nullptr;
+    int *tile_status = nullptr;
+    long long *tile_value = nullptr;
+    int32_t max_tiles = 0;
+
+    // host-input streaming (ecc_compute_host), allocated on first use
+    unsigned char *stage = nullptr;
+    size_t stage_bytes = 0;
+    long long *stage_ecc = nullptr;
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t chunk_ev[ecc::kMaxChunkEvents] = {};
+
+    // tile parameter per (ndim, esize) key chosen by the autotuner
+    int tuned[4] = {0, 0, 0, 0};
+
+    ecc::BatchState *batch = nullptr;
+
+    // ECC_FLAG_TIME_KERNELS: event pairs around stencil launches
+    std::vector<cudaEvent_t> time_ev;
+    size_t time_used = 0;
+
+    ecc_status allocate();
+    void release();
+    void autotune();
+    ecc_status ensure_stage(int64_t bytes);
+    int tune_param(const ecc::Geom &g) const;
+    ecc::ScanWs scan_ws() const
+    {
+        return ecc::ScanWs{scan_counters, scan_counters + 1, tile_status, tile_value, max_tiles};
+    }
+};
+
+namespace ecc {
+
+ecc_status image_geom(const ecc_image *img, int32_t want_dtype, int64_t max_voxels, Geom *g, int64_t *voxels,
+                      bool allow_null_data);
+cudaError_t launch_stencil(ecc_plan_s *p, const Geom &g, int64_t ob, int64_t oe, const HistDst &h,
+                           cudaStream_t s);
+void release_batch(ecc_plan_s *p);
+
+}  // namespace ecc

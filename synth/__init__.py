@@ -108,14 +108,15 @@ def add_blobs(vol: torch.Tensor, count: int, seed: int, r_range=(3, 12), v_range
     values = rng.integers(v_range[0], v_range[1] + 1, size=count)
     centres = np.stack([rng.integers(0, d, size=count) for d in dims], axis=1)
     dev = vol.device
+    out = vol.to(torch.int32)  # index_put is not implemented for uint16
     for r, v, c in zip(radii.tolist(), values.tolist(), centres.tolist()):
         sl = tuple(slice(max(0, ci - r), min(d, ci + r + 1)) for ci, d in zip(c, dims))
         grids = torch.meshgrid(*[torch.arange(s.start, s.stop, device=dev) - ci for s, ci in zip(sl, c)],
                                indexing="ij")
         inside = sum(g * g for g in grids) <= r * r
-        view = vol[sl]
-        view[inside] = torch.tensor(v, dtype=torch.int32, device=dev).to(vol.dtype)
-    return vol
+        view = out[sl]
+        view[inside] = v
+    return out.to(vol.dtype)
 
 
 # --- the five benchmark configurations ---------------------------------------

@@ -1,0 +1,172 @@
+"""Batched path (ecc_compute_batch) and serving loop (ecc_submit) against the
+oracle: every image's ECC must be identical alone, in a batch, and in the
+served mix (tolerance 0)."""
+import threading
+
+import numpy as np
+import pytest
+
+import oracle
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+
+def ecc_mod():
+    import paper_2203_09087_gb300 as ecc
+    return ecc
+
+
+def _mixed_images(n, seed, dtype=np.uint8, max2d=300, max3d=48):
+    rng = np.random.default_rng(seed)
+    imgs = []
+    hi = 255 if dtype == np.uint8 else 65535
+    for i in range(n):
+        if rng.uniform() < 0.7:
+            shape = tuple(rng.integers(1, max2d + 1, size=2))
+        else:
+            shape = tuple(rng.integers(1, max3d + 1, size=3))
+        levels = int(rng.choice([2, 5, hi + 1]))
+        imgs.append(rng.integers(0, levels, size=shape).astype(dtype))
+    return imgs
+
+
+@pytest.mark.parametrize("flags", [0, 0x40])
+@pytest.mark.parametrize("mode", [0, 1])
+def test_batch_uneven_u8(flags, mode):
+    ecc = ecc_mod()
+    imgs = _mixed_images(150, seed=1 + mode)
+    plan = ecc.ecc_plan("u8", 0, 255, complex_mode=mode, max_images=len(imgs),
+                        max_voxels=sum(i.size for i in imgs), flags=flags)
+    got = ecc.ecc_compute_batch(plan, [torch.from_numpy(i).cuda() for i in imgs])
+    ecc.ecc_status_get(plan)
+    got = got.cpu().numpy()
+    om = oracle.VERTEX if mode == 0 else oracle.TOPCELL
+    for k, img in enumerate(imgs):
+        assert np.array_equal(got[k], oracle.ecc(img, 0, 255, om)), (k, img.shape)
+
+
+def test_batch_u16_and_subrange():
+    ecc = ecc_mod()
+    rng = np.random.default_rng(5)
+    imgs = [rng.integers(1000, 1400, size=tuple(rng.integers(1, 60, size=int(rng.integers(2, 4)))),
+                         dtype=np.uint16) for _ in range(40)]
+    plan = ecc.ecc_plan("u16", 990, 1410, max_images=64, max_voxels=1 << 24)
+    got = ecc.ecc_compute_batch(plan, [torch.from_numpy(i).cuda() for i in imgs]).cpu().numpy()
+    ecc.ecc_status_get(plan)
+    for k, img in enumerate(imgs):
+        assert np.array_equal(got[k], oracle.ecc(img, 990, 1410))
+
+
+def test_batch_repeated_and_resized():
+    """The same plan serves batches of different sizes back to back."""
+    ecc = ecc_mod()
+    plan = ecc.ecc_plan("u8", 0, 255, max_images=80, max_voxels=1 << 24)
+    for seed, n in [(11, 80), (12, 3), (13, 80), (14, 1)]:
+        imgs = _mixed_images(n, seed)
+        got = ecc.ecc_compute_batch(plan, [torch.from_numpy(i).cuda() for i in imgs]).cpu().numpy()
+        for k, img in enumerate(imgs):
+            assert np.array_equal(got[k], oracle.ecc(img, 0, 255))
+
+
+def test_batch_full_size_config4_sampled():
+    """The uneven 4096 + 256 batch at full size: every row equals the
+    one-launch-per-image path; a seeded sample of rows equals the oracle."""
+    import synth
+    ecc = ecc_mod()
+    specs = synth.batch_specs()
+    imgs = synth.batch_images(specs, device="cuda")
+    total = sum(i.numel() for i in imgs)
+    plan_b = ecc.ecc_plan("u8", 0, 255, max_images=len(imgs), max_voxels=total)
+    plan_p = ecc.ecc_plan("u8", 0, 255, max_images=len(imgs), max_voxels=total, flags=ecc.ECC_FLAG_BATCH_PER_IMAGE)
+    got_b = ecc.ecc_compute_batch(plan_b, imgs).cpu().numpy()
+    got_p = ecc.ecc_compute_batch(plan_p, imgs).cpu().numpy()
+    ecc.ecc_status_get(plan_b)
+    assert np.array_equal(got_b, got_p)
+    rng = np.random.default_rng(99)
+    for k in rng.choice(len(imgs), size=40, replace=False).tolist() + [len(imgs) - 1]:
+        host = imgs[k].cpu().numpy()
+        assert np.array_equal(got_b[k], oracle.ecc(host, 0, 255)), k
+
+
+# ------------------------------------------------------------------ serving
+
+def _server(ecc, budget=1 << 30, streams=4, max_batch=16):
+    return ecc.ecc_server_create(budget, n_streams=streams, max_batch=max_batch)
+
+
+def test_served_results_equal_alone_and_oracle():
+    ecc = ecc_mod()
+    rng = np.random.default_rng(21)
+    jobs = []
+    for i in range(120):
+        dt = np.uint8 if rng.uniform() < 0.7 else np.uint16
+        hi = 255 if dt == np.uint8 else 65535
+        shape = tuple(rng.integers(1, 200, size=2)) if rng.uniform() < 0.6 else tuple(rng.integers(1, 40, size=3))
+        img = rng.integers(0, hi + 1, size=shape).astype(dt)
+        mode = int(rng.integers(0, 2))
+        jobs.append((img, hi, mode))
+    srv = _server(ecc)
+    outs = [np.zeros(hi + 1, np.int64) for _, hi, _ in jobs]
+    dev = [torch.from_numpy(img).cuda() if k % 2 else None for k, (img, _, _) in enumerate(jobs)]
+    tickets = [None] * len(jobs)
+
+    def submit(lo_k, hi_k):
+        for k in range(lo_k, hi_k):
+            img, hi, mode = jobs[k]
+            src = dev[k] if dev[k] is not None else img
+            tickets[k] = ecc.ecc_submit(srv, src, 0, hi, mode, out=outs[k])
+
+    ts = [threading.Thread(target=submit, args=(a, a + 30)) for a in range(0, 120, 30)]
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join()
+    for k in range(len(jobs)):
+        assert ecc.ecc_wait(srv, tickets[k], 60_000_000) == ecc.ECC_OK
+    stats = ecc.ecc_server_stats(srv)
+    assert stats["jobs"] == len(jobs) and stats["p99_us"] >= stats["p50_us"] > 0
+    ecc.ecc_server_destroy(srv)
+    for k, (img, hi, mode) in enumerate(jobs):
+        om = oracle.VERTEX if mode == 0 else oracle.TOPCELL
+        assert np.array_equal(outs[k], oracle.ecc(img, 0, hi, om)), k
+    # the same job alone gives the same bits
+    srv1 = _server(ecc, streams=1, max_batch=1)
+    img, hi, mode = jobs[7]
+    alone = np.zeros(hi + 1, np.int64)
+    t = ecc.ecc_submit(srv1, img, 0, hi, mode, out=alone)
+    assert ecc.ecc_wait(srv1, t) == ecc.ECC_OK
+    ecc.ecc_server_destroy(srv1)
+    assert np.array_equal(alone, outs[7])
+
+
+def test_budget_admission_and_errors():
+    ecc = ecc_mod()
+    img = np.random.default_rng(1).integers(0, 256, size=(64, 64, 64), dtype=np.uint8)  # 256 KiB per job
+    srv = _server(ecc, budget=600_000, streams=2, max_batch=4)   # room for two jobs at a time
+    outs = [np.zeros(256, np.int64) for _ in range(10)]
+    tickets = [ecc.ecc_submit(srv, img, 0, 255, out=o) for o in outs]
+    for t in tickets:
+        assert ecc.ecc_wait(srv, t, 60_000_000) == ecc.ECC_OK
+    want = oracle.ecc(img, 0, 255)
+    for o in outs:
+        assert np.array_equal(o, want)
+    assert ecc.ecc_server_stats(srv)["peak_bytes"] <= 600_000
+    big = np.zeros((100, 100, 100), np.uint8)   # 1 MB alone exceeds the budget
+    with pytest.raises(ecc.EccError) as ei:
+        ecc.ecc_submit(srv, big, 0, 255)
+    assert ei.value.status == ecc.ECC_E_NOMEM
+    with pytest.raises(ecc.EccError):
+        ecc.ecc_submit(srv, img, 10, 5)
+    ecc.ecc_server_destroy(srv)
+
+
+def test_destroy_with_cancel_drains_or_cancels():
+    ecc = ecc_mod()
+    img = np.random.default_rng(2).integers(0, 256, size=(128, 256, 256), dtype=np.uint8)
+    srv = _server(ecc, budget=20_000_000, streams=1, max_batch=1)
+    tickets = [ecc.ecc_submit(srv, img, 0, 255) for _ in range(20)]
+    srv.close(cancel=True)
+    # nothing hangs; the handle is gone
+    assert not srv.handle.value
