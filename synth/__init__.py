@@ -64,12 +64,18 @@ def _smooth_axis(f: torch.Tensor, taps: torch.Tensor, axis: int) -> torch.Tensor
     g = f.movedim(axis, -1)
     shp = g.shape
     g = g.reshape(-1, 1, n)
-    if r >= n:  # reflect padding needs r < n; fall back to replicate for tiny axes
-        g = torch.nn.functional.pad(g, (r, r), mode="replicate")
-    else:
-        g = torch.nn.functional.pad(g, (r, r), mode="reflect")
-    g = torch.nn.functional.conv1d(g, taps.to(g.device).view(1, 1, -1))
-    return g.reshape(shp).movedim(-1, axis)
+    if r >= n:  # reflect padding needs r < n; replicate the edge values for tiny axes
+        left = g[..., :1].expand(-1, -1, r)
+        right = g[..., -1:].expand(-1, -1, r)
+    else:       # reflect (edge not repeated), built with flips: no batch-size limit
+        left = g[..., 1:r + 1].flip(-1)
+        right = g[..., n - 1 - r:n - 1].flip(-1)
+    g = torch.cat([left, g, right], dim=-1)
+    out = torch.empty(g.shape[0], 1, n, dtype=g.dtype, device=g.device)
+    step = 1 << 20  # bound the rows per convolution call
+    for i in range(0, g.shape[0], step):
+        out[i:i + step] = torch.nn.functional.conv1d(g[i:i + step], taps.to(g.device).view(1, 1, -1))
+    return out.reshape(shp).movedim(-1, axis)
 
 
 def smooth(f: torch.Tensor, sigma: float) -> torch.Tensor:

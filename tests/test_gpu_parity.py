@@ -60,6 +60,38 @@ def test_uniform_u8(shape, mode, kernel):
     assert np.array_equal(_run(_gpu(img), 0, 255, mode, kernel), _expect(img, 0, 255, mode))
 
 
+# 3D shapes whose rows are 16-byte aligned take the TMA-staged bit-sliced kernel
+TMA_SHAPES = [(40, 64, 64), (33, 48, 96), (7, 35, 160), (100, 31, 32), (3, 64, 208), (65, 100, 112),
+              (1, 80, 48), (2, 2, 16), (31, 61, 512), (9, 33, 1008)]
+
+
+@pytest.mark.parametrize("mode", list(MODES))
+@pytest.mark.parametrize("shape", TMA_SHAPES)
+@pytest.mark.parametrize("levels", [3, 256])
+def test_tma_path_u8(shape, mode, levels):
+    rng = np.random.default_rng(sum(shape) + levels)
+    img = rng.integers(0, levels, size=shape, dtype=np.uint8)
+    assert np.array_equal(_run(_gpu(img), 0, 255, mode), _expect(img, 0, 255, mode))
+
+
+@pytest.mark.parametrize("mode", list(MODES))
+@pytest.mark.parametrize("shape", [(20, 40, 72), (9, 33, 136), (50, 17, 8), (4, 70, 256)])
+@pytest.mark.parametrize("levels", [5, 65536])
+def test_tma_path_u16(shape, mode, levels):
+    rng = np.random.default_rng(sum(shape) + levels)
+    img = rng.integers(0, levels, size=shape).astype(np.uint16)
+    assert np.array_equal(_run(_gpu(img), 0, 65535, mode), _expect(img, 0, 65535, mode))
+
+
+@pytest.mark.parametrize("mode", list(MODES))
+def test_tma_path_pitched_view(mode):
+    rng = np.random.default_rng(6)
+    big = rng.integers(0, 7, size=(40, 90, 256), dtype=np.uint8)
+    view = _gpu(big)[3:37, 2:85, 32:232]   # 16-byte aligned start, pitches 256 and 90*256
+    want = _expect(np.ascontiguousarray(big[3:37, 2:85, 32:232]), 0, 255, mode)
+    assert np.array_equal(_run(view, 0, 255, mode), want)
+
+
 @pytest.mark.parametrize("kernel", list(KERNELS))
 @pytest.mark.parametrize("mode", list(MODES))
 @pytest.mark.parametrize("shape", [(61, 70), (5, 66, 40), (33, 31, 130)])
