@@ -155,6 +155,29 @@ ecc_status ecc_compute_host(ecc_plan_t plan, const ecc_image *h_img, int64_t *h_
 ecc_status ecc_compute_batch(ecc_plan_t plan, int32_t n, const ecc_image *host_descs,
                              int64_t *d_ecc, void *stream);
 
+/* ECC of one image without allocating anything: for callers that cannot
+ * allocate device memory once running -- a real-time pipeline whose device
+ * memory budget is fixed at start-up, code running inside another
+ * framework's memory pool or allocator callback, or a process whose device
+ * memory that pool has fully reserved.  A plan allocates its workspace with
+ * cudaMalloc; this call instead uses one fixed scratch array of the library
+ * (an int64 accumulator of 65536 levels plus scan state, about 513 KiB),
+ * which every GPU that loads the library holds until the process exits.
+ * The paper has no counterpart: it is a deployment variant of ecc_compute.
+ *   img, d_ecc, d_vcec   as in ecc_compute (device buffers owned by the caller)
+ *   lo, hi, complex_mode as in ecc_plan_desc; hi - lo + 1 must be <= 65536
+ *   flags                ECC_FLAG_NO_RANGE_CHECK and ECC_FLAG_KERNEL_DIRECT honoured
+ * Calls no cudaMalloc, cudaFree or allocating library routine.  The first
+ * call on a device looks the scratch array up and clears it (set-up), so it
+ * should come before any stream capture.  Each call clears what must start
+ * at zero; all calls on a device share the array, so calls whose work
+ * overlaps on the GPU (other streams, other host threads) race and corrupt
+ * each other's results.  Synchronous: returns after the work on `stream`
+ * finished, with device-detected errors (ECC_E_RANGE, ECC_E_TIMEOUT).
+ * Errors: ECC_E_INVALID (including more than 65536 levels), ECC_E_CUDA. */
+ecc_status ecc_compute_noalloc(const ecc_image *img, int32_t lo, int32_t hi, int32_t complex_mode,
+                               uint32_t flags, int64_t *d_ecc, int64_t *d_vcec, void *stream);
+
 /* Waits for the plan's work on `stream`, then returns and clears the device
  * status word: ECC_OK, ECC_E_RANGE (a value outside [lo, hi] was seen) or
  * ECC_E_TIMEOUT (a bounded device-side wait gave up). */

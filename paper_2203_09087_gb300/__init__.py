@@ -40,6 +40,7 @@ from ._binding import (  # noqa: F401
     ecc_compute,
     ecc_compute_batch,
     ecc_compute_host,
+    ecc_compute_noalloc,
     ecc_last_error,
     ecc_plan,
     ecc_plan_destroy,

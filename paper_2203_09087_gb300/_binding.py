@@ -59,6 +59,8 @@ _SIGNATURES = {
     "ecc_compute": (ctypes.c_int, [_VP, ctypes.POINTER(EccImage), _VP, _VP, _VP]),
     "ecc_compute_host": (ctypes.c_int, [_VP, ctypes.POINTER(EccImage), _VP, _VP]),
     "ecc_compute_batch": (ctypes.c_int, [_VP, _I32, ctypes.POINTER(EccImage), _VP, _VP]),
+    "ecc_compute_noalloc": (ctypes.c_int, [ctypes.POINTER(EccImage), _I32, _I32, _I32, ctypes.c_uint32, _VP, _VP,
+                                           _VP]),
     "ecc_status_get": (ctypes.c_int, [_VP, _VP]),
     "ecc_plan_kernel_time": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_I64)]),
     "ecc_last_error": (ctypes.c_char_p, []),
@@ -270,6 +272,28 @@ def ecc_plan_kernel_time(plan: Plan):
     n = ctypes.c_int64()
     _check(library().ecc_plan_kernel_time(plan.handle, ctypes.byref(ms), ctypes.byref(n)))
     return ms.value, n.value
+
+
+def ecc_compute_noalloc(image, lo: int = 0, hi: int | None = None, complex_mode: int = ECC_VERTEX_MAX,
+                        out=None, vcec_out=None, flags: int = 0, stream=None):
+    """ECC of one CUDA image with no device allocation inside the library
+    (fixed scratch array; synchronous).  ``out`` must be given by callers that
+    cannot let this binding allocate it."""
+    import torch
+    d = image_desc(image)
+    if hi is None:
+        hi = 255 if d.dtype == ECC_U8 else 65535
+    n = hi - lo + 1
+    if out is None:
+        out = torch.empty(n, dtype=torch.int64, device=image.device)
+    _check_out(out, n)
+    vptr = None
+    if vcec_out is not None:
+        _check_out(vcec_out, n)
+        vptr = vcec_out.data_ptr()
+    _check(library().ecc_compute_noalloc(ctypes.byref(d), int(lo), int(hi), int(complex_mode), int(flags),
+                                         out.data_ptr(), vptr, _stream_handle(stream)))
+    return out
 
 
 def ecc_status_get(plan: Plan, stream=None) -> int:
