@@ -1,19 +1,454 @@
-// ecc_batch.cu -- ecc_compute_batch: many images of uneven shapes.
+// ecc_batch.cu -- ecc_compute_batch: thousands of images of uneven shapes.
+//
+// Table 3 of the paper shows per-image GPU overhead amortizing over many
+// files; Sec. 3.4 reassigns free blocks to new chunks.  Here the whole batch
+// is one persistent kernel:
+//
+//  1. the host packs one descriptor per image into pinned staging memory;
+//  2. a one-CTA kernel turns the descriptors into a device-side work list:
+//     per image, its number of tiles (2D: 960 columns x `chunk` rows; 3D:
+//     30x30 voxels x `chunk` planes) and the exclusive prefix of the counts;
+//  3. the persistent kernel's warps pull tiles from an atomic counter, find
+//     their image by binary search over the prefix, and walk the tile with the
+//     bit-sliced walkers (ecc_walk.cuh), reading rows straight from global
+//     memory (any pitch, any alignment); each warp accumulates into its own
+//     shared-memory histogram, flushed into image i's bins (offset i*nbins)
+//     whenever the warp moves to another image;
+//  4. one segmented scan turns all histograms into ECCs.
+//
+// Steps 1-4 are captured once per plan into a CUDA graph whose parameters
+// live in device memory; each call updates the copy and scan nodes (source
+// staging buffer, number of images, output pointer) and relaunches the graph.
+// ECC_FLAG_BATCH_PER_IMAGE keeps the plain one-launch-per-image path for
+// comparison.
 #include <cuda_runtime.h>
 
 #include <vector>
 
 #include "ecc_plan.h"
+#include "ecc_walk.cuh"
 
 namespace ecc {
 
-struct BatchState {
-    int unused = 0;
+struct BatchImage {  // 64 bytes
+    const unsigned char *data;
+    int64_t nx, ny, nz;
+    int64_t pitch_y, pitch_z;
+    int32_t ndim, esize;
 };
+
+struct BatchHeader {
+    int32_t n;
+    int32_t pad[3];
+};
+
+struct BatchState {
+    int32_t cap = 0;
+    // device: header + descriptors, work-list prefix [cap + 1], counter
+    unsigned char *d_desc = nullptr;
+    long long *d_start = nullptr;
+    unsigned int *d_counter = nullptr;
+    // pinned staging (double-buffered) and the event of each buffer's last use
+    unsigned char *h_stage[2] = {nullptr, nullptr};
+    cudaEvent_t stage_ev[2] = {nullptr, nullptr};
+    int next = 0;
+    // the captured graph and the nodes updated per call
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraphNode_t copy_node = nullptr, scan_node = nullptr;
+    ScanArgs scan{};            // kernel arguments of the scan node (output set per call)
+    void *scan_argv[1] = {nullptr};
+    unsigned scan_grid = 0;
+    int persistent_ctas = 0;
+    int chunk2d = 32, chunk3d = 16;
+};
+
+namespace {
+
+constexpr int kBatchWarps = 4;
+constexpr int kTile2d = 32 * 30;  // columns per 2D tile (one warp of windows)
+constexpr int kOut3 = 30;         // x and y extent of a 3D tile
+
+struct BatchArgs {
+    const BatchHeader *hdr;
+    const BatchImage *img;
+    long long *start;  // [n + 1] exclusive prefix of tile counts
+    unsigned int *counter;
+    unsigned long long *acc;
+    int32_t lo, nbins;
+    int32_t chunk2d, chunk3d;
+    int32_t smem_hist, range_check;
+    unsigned int *status;
+};
+
+__device__ __forceinline__ long long tiles_of(const BatchImage &im, int chunk2d, int chunk3d)
+{
+    if (im.ndim == 2) {
+        const long long tx = (im.nx + kTile2d - 1) / kTile2d;
+        const long long ty = (im.ny + chunk2d - 1) / chunk2d;
+        return tx * ty;
+    }
+    const long long tx = (im.nx + kOut3 - 1) / kOut3;
+    const long long ty = (im.ny + kOut3 - 1) / kOut3;
+    const long long tz = (im.nz + chunk3d - 1) / chunk3d;
+    return tx * ty * tz;
+}
+
+// Work list: exclusive prefix of per-image tile counts (one CTA of 1024).
+__global__ void __launch_bounds__(1024) build_worklist(BatchArgs a)
+{
+    __shared__ long long s_part[32];
+    __shared__ long long s_carry;
+    const int n = a.hdr->n;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) {
+        s_carry = 0;
+        *a.counter = 0u;
+    }
+    __syncthreads();
+    for (int base = 0; base < n; base += 1024) {
+        const int i = base + tid;
+        long long c = i < n ? tiles_of(a.img[i], a.chunk2d, a.chunk3d) : 0;
+        long long x = c;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const long long y = __shfl_up_sync(0xffffffffu, x, off);
+            if (lane >= off) x += y;
+        }
+        if (lane == 31) s_part[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            long long p = s_part[lane];
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const long long y = __shfl_up_sync(0xffffffffu, p, off);
+                if (lane >= off) p += y;
+            }
+            s_part[lane] = p;
+        }
+        __syncthreads();
+        const long long incl = x + (warp ? s_part[warp - 1] : 0) + s_carry;
+        if (i < n) a.start[i] = incl - c;
+        __syncthreads();
+        if (tid == 1023) s_carry = incl;
+        __syncthreads();
+    }
+    if (tid == 0) a.start[n] = s_carry;
+}
+
+template <int K, bool TOP>
+struct Emitter {
+    int *hist;                 // this warp's shared bins, or null for global
+    unsigned long long *acc;   // this image's global bins
+    int lo, nbins, range_check;
+    unsigned int *status;
+    __device__ __forceinline__ void add(int v, int kap) const
+    {
+        const int bin = v - lo;
+        if (range_check && (unsigned)bin >= (unsigned)nbins) {
+            atomicOr(status, DEV_RANGE);
+            return;
+        }
+        if (hist)
+            atomicAdd(&hist[bin], kap);
+        else
+            atomicAdd(acc + bin, (unsigned long long)(long long)kap);
+    }
+};
+
+template <int K, bool TOP, int ND>
+__device__ void run_tile(const BatchArgs &a, const BatchImage &im, long long local, const Emitter<K, TOP> &em,
+                         int lane)
+{
+    constexpr int NWORDS = K;
+    const int64_t row_bytes = im.nx * (K / 8);
+    if (ND == 2) {
+        const long long tx = (im.nx + kTile2d - 1) / kTile2d;
+        const int64_t xt = local % tx, yc = local / tx;
+        const int64_t yb = yc * a.chunk2d;
+        const int64_t ye = yb + a.chunk2d < im.ny ? yb + a.chunk2d : im.ny;
+        const int64_t xw = xt * kTile2d + 30 * lane - 1;
+        const int64_t first = xw * (K / 8);
+        const uint32_t xex = walk::x_exist_mask(xw, im.nx);
+        const uint32_t out_x = xex & 0x7ffffffeu;
+        auto fetch = [&](int64_t y, uint32_t *w) -> int {
+            if (y < 0 || y >= im.ny || !xex) {
+#pragma unroll
+                for (int i = 0; i <= NWORDS; ++i) w[i] = 0;
+                return 0;
+            }
+            return walk::load_row_words<NWORDS>(im.data + y * im.pitch_y, row_bytes, first, w);
+        };
+        uint32_t wn[NWORDS + 1], P[K];
+        int sh = fetch(yb - 1, wn);
+        walk::planes_from_words<K>(wn, sh, P);
+        walk::Walk2d<K, TOP> wk;
+        wk.begin(P, xex);
+        sh = fetch(yb, wn);
+        for (int64_t y1 = yb; y1 <= ye; ++y1) {
+            uint32_t B[K];
+            walk::planes_from_words<K>(wn, sh, B);
+            if (y1 + 1 <= ye) sh = fetch(y1 + 1, wn);
+            wk.step(B, y1 < im.ny, y1 - 1 >= 0, y1 - 1 >= yb, out_x,
+                    [&](uint32_t m, const uint32_t *Q, const uint32_t *F, const uint32_t *A) {
+                        while (m) {
+                            const int i = __ffs(m) - 1;
+                            m &= m - 1;
+                            em.add(bs::bits_at<K>(A, i), 1 + bs::bits_at<3>(Q, i) - bs::bits_at<3>(F, i));
+                        }
+                    });
+        }
+    } else {
+        const long long tx = (im.nx + kOut3 - 1) / kOut3;
+        const long long ty = (im.ny + kOut3 - 1) / kOut3;
+        const int64_t xt = local % tx;
+        const int64_t r = local / tx;
+        const int64_t yt = r % ty, zc = r / ty;
+        const int64_t zb = zc * a.chunk3d;
+        const int64_t ze = zb + a.chunk3d < im.nz ? zb + a.chunk3d : im.nz;
+        const int64_t y = yt * kOut3 - 1 + lane;
+        const int64_t xw = xt * kOut3 - 1;
+        const int64_t first = xw * (K / 8);
+        const uint32_t xex = walk::x_exist_mask(xw, im.nx);
+        const bool row_ok = y >= 0 && y < im.ny;
+        const uint32_t out_x = (lane >= 1 && lane <= kOut3 && y < im.ny) ? (xex & 0x7ffffffeu) : 0u;
+        auto fetch = [&](int64_t z, uint32_t *w) -> int {
+            if (z < 0 || z >= im.nz || !row_ok) {
+#pragma unroll
+                for (int i = 0; i <= NWORDS; ++i) w[i] = 0;
+                return 0;
+            }
+            return walk::load_row_words<NWORDS>(im.data + z * im.pitch_z + y * im.pitch_y, row_bytes, first, w);
+        };
+        const int64_t y0 = yt * kOut3 - 1;
+        const bool inner_xy = xw >= 0 && xw + 32 <= im.nx && y0 >= 0 && y0 + 31 < im.ny;
+        walk::Walk3d<K, TOP> wk;
+        wk.begin(xex, y - 1 >= 0 && y - 1 < im.ny, y + 1 >= 0 && y + 1 < im.ny);
+        auto emit = [&](uint32_t m, const uint32_t *S, const uint32_t *N, const uint32_t *A) {
+            while (m) {
+                const int i = __ffs(m) - 1;
+                m &= m - 1;
+                int kap = 1 + bs::bits_at<4>(S, i) - bs::bits_at<4>(N, i);
+                if (TOP) kap = -kap;  // (-1)^d, d = 3
+                em.add(bs::bits_at<K>(A, i), kap);
+            }
+        };
+        uint32_t wn[NWORDS + 1];
+        walk::Rows3<K> r0, r1;
+        int sh = fetch(zb - 1, wn);
+        walk::planes_from_words<K>(wn, sh, r0.P);
+        walk::complete_rows<K>(r0);
+        sh = fetch(zb, wn);
+        int64_t z1 = zb;
+        auto load_next = [&](walk::Rows3<K> &r) {   // plane z1 from the prefetched words
+            walk::planes_from_words<K>(wn, sh, r.P);
+            if (z1 + 1 <= ze) sh = fetch(z1 + 1, wn);
+            walk::complete_rows<K>(r);
+        };
+        auto advance = [&](const walk::Rows3<K> &cur, const walk::Rows3<K> &nxt) {
+            const bool zp = z1 < im.nz, zok = z1 - 1 >= 0;
+            const bool emit_z = z1 - 1 >= zb;
+            if (inner_xy && zp && zok)
+                wk.template step<false>(cur, nxt, zp, zok, emit_z, out_x, emit);
+            else
+                wk.template step<true>(cur, nxt, zp, zok, emit_z, out_x, emit);
+            ++z1;
+        };
+        for (;;) {
+            load_next(r1);
+            advance(r0, r1);
+            if (z1 > ze) break;
+            load_next(r0);
+            advance(r1, r0);
+            if (z1 > ze) break;
+        }
+    }
+}
+
+template <int K, bool TOP>
+__global__ void __launch_bounds__(kBatchWarps * 32) batch_kernel(BatchArgs a)
+{
+    extern __shared__ __align__(16) int bhist[];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    int *hist = a.smem_hist ? bhist + warp * a.nbins : nullptr;
+    if (hist)
+        for (int i = lane; i < a.nbins; i += 32) hist[i] = 0;
+    __syncwarp();
+    const int n = a.hdr->n;
+    const long long total = a.start[n];
+    int cur = -1;  // image whose bins this warp's shared histogram holds
+    auto flush = [&]() {
+        if (hist && cur >= 0) {
+            __syncwarp();
+            unsigned long long *dst = a.acc + (size_t)cur * a.nbins;
+            for (int i = lane; i < a.nbins; i += 32) {
+                const int v = hist[i];
+                if (v) {
+                    atomicAdd(dst + i, (unsigned long long)(long long)v);
+                    hist[i] = 0;
+                }
+            }
+            __syncwarp();
+        }
+    };
+    for (;;) {
+        long long item = 0;
+        if (lane == 0) item = (long long)atomicAdd(a.counter, 1u);
+        item = __shfl_sync(0xffffffffu, item, 0);
+        if (item >= total) break;
+        // image owning this tile: last i with start[i] <= item
+        int lo = 0, hi = n - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (a.start[mid] <= item)
+                lo = mid;
+            else
+                hi = mid - 1;
+        }
+        if (lo != cur) {
+            flush();
+            cur = lo;
+        }
+        const BatchImage im = a.img[lo];
+        Emitter<K, TOP> em{hist, a.acc + (size_t)lo * a.nbins, a.lo, a.nbins, a.range_check, a.status};
+        if (im.ndim == 2)
+            run_tile<K, TOP, 2>(a, im, item - a.start[lo], em, lane);
+        else
+            run_tile<K, TOP, 3>(a, im, item - a.start[lo], em, lane);
+    }
+    flush();
+}
+
+template <int K, bool TOP>
+cudaError_t batch_instance(void **fn, size_t smem, int *per_sm)
+{
+    auto kern = batch_kernel<K, TOP>;
+    *fn = reinterpret_cast<void *>(kern);
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, kern, kBatchWarps * 32, smem);
+}
+
+cudaError_t capture_graph(ecc_plan_s *p, BatchState *b)
+{
+    const bool top = p->d.complex_mode == ECC_TOPCELL_MIN;
+    const int K = p->d.dtype == ECC_U16 ? 16 : 8;
+    const bool smem_hist = (size_t)kBatchWarps * p->nbins * 4 <= 96 * 1024;
+    const size_t smem = smem_hist ? (size_t)kBatchWarps * p->nbins * 4 : 0;
+    void *fn = nullptr;
+    int per_sm = 0;
+    cudaError_t e = K == 8 ? (top ? batch_instance<8, true>(&fn, smem, &per_sm) : batch_instance<8, false>(&fn, smem, &per_sm))
+                           : (top ? batch_instance<16, true>(&fn, smem, &per_sm) : batch_instance<16, false>(&fn, smem, &per_sm));
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorNotSupported;
+    b->persistent_ctas = p->num_sms * per_sm;
+
+    static BatchArgs args;  // copied into the graph at capture
+    args = BatchArgs{};
+    args.hdr = reinterpret_cast<const BatchHeader *>(b->d_desc);
+    args.img = reinterpret_cast<const BatchImage *>(b->d_desc + sizeof(BatchHeader));
+    args.start = b->d_start;
+    args.counter = b->d_counter;
+    args.acc = p->acc;
+    args.lo = p->d.lo;
+    args.nbins = p->nbins;
+    args.chunk2d = b->chunk2d;
+    args.chunk3d = b->chunk3d;
+    args.smem_hist = smem_hist;
+    args.range_check = !(p->d.flags & ECC_FLAG_NO_RANGE_CHECK);
+    args.status = p->status;
+
+    e = cudaGraphCreate(&b->graph, 0);
+    if (e != cudaSuccess) return e;
+    // copy node: staging -> device descriptors (parameters replaced per call)
+    cudaMemcpy3DParms cp{};
+    cp.srcPtr = make_cudaPitchedPtr(b->h_stage[0], 64, 64, 1);
+    cp.dstPtr = make_cudaPitchedPtr(b->d_desc, 64, 64, 1);
+    cp.extent = make_cudaExtent(64, 1, 1);
+    cp.kind = cudaMemcpyHostToDevice;
+    e = cudaGraphAddMemcpyNode(&b->copy_node, b->graph, nullptr, 0, &cp);
+    if (e != cudaSuccess) return e;
+    // work-list kernel
+    cudaGraphNode_t build_node, batch_node;
+    void *bargs[] = {&args};
+    cudaKernelNodeParams kp{};
+    kp.func = reinterpret_cast<void *>(build_worklist);
+    kp.gridDim = dim3(1);
+    kp.blockDim = dim3(1024);
+    kp.kernelParams = bargs;
+    e = cudaGraphAddKernelNode(&build_node, b->graph, &b->copy_node, 1, &kp);
+    if (e != cudaSuccess) return e;
+    // persistent kernel
+    kp.func = fn;
+    kp.gridDim = dim3((unsigned)b->persistent_ctas);
+    kp.blockDim = dim3(kBatchWarps * 32);
+    kp.sharedMemBytes = (unsigned)smem;
+    e = cudaGraphAddKernelNode(&batch_node, b->graph, &build_node, 1, &kp);
+    if (e != cudaSuccess) return e;
+    // segmented scan (output pointer set per call; image count read on the device)
+    b->scan = ScanArgs{};
+    b->scan.acc = p->acc;
+    b->scan.nbins = p->nbins;
+    b->scan.n = (int64_t)p->d.max_images * p->nbins;
+    b->scan.ws = p->scan_ws();
+    b->scan.status = p->status;
+    b->scan.n_seg_dev = reinterpret_cast<const int *>(b->d_desc);  // BatchHeader::n
+    b->scan_grid = (unsigned)scan_tiles(p->d.max_images, p->nbins);
+    b->scan.ntiles = (int32_t)b->scan_grid;
+    b->scan_argv[0] = &b->scan;
+    kp = cudaKernelNodeParams{};
+    kp.func = const_cast<void *>(scan_kernel_entry());
+    kp.gridDim = dim3(b->scan_grid);
+    kp.blockDim = dim3(kScanThreads);
+    kp.kernelParams = b->scan_argv;
+    e = cudaGraphAddKernelNode(&b->scan_node, b->graph, &batch_node, 1, &kp);
+    if (e != cudaSuccess) return e;
+    e = cudaGraphInstantiate(&b->exec, b->graph, 0);
+    return e;
+}
+
+ecc_status ensure_batch(ecc_plan_s *p)
+{
+    if (p->batch) return ECC_OK;
+    auto *b = new BatchState();
+    b->cap = p->d.max_images;
+    b->chunk2d = p->tuned_batch[0] > 0 ? p->tuned_batch[0] : 32;
+    b->chunk3d = p->tuned_batch[1] > 0 ? p->tuned_batch[1] : 16;
+    const size_t desc_bytes = sizeof(BatchHeader) + sizeof(BatchImage) * (size_t)b->cap;
+    cudaError_t e = cudaMalloc(&b->d_desc, desc_bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_start, sizeof(long long) * ((size_t)b->cap + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_counter, 256);
+    for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
+        e = cudaMallocHost(&b->h_stage[i], desc_bytes);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->stage_ev[i], cudaEventDisableTiming);
+    }
+    p->batch = b;
+    if (e == cudaSuccess) e = capture_graph(p, b);
+    if (e != cudaSuccess) {
+        release_batch(p);
+        return cuda_fail(e, "ecc_compute_batch: batch state set-up");
+    }
+    return ECC_OK;
+}
+
+}  // namespace
 
 void release_batch(ecc_plan_s *p)
 {
-    delete p->batch;
+    BatchState *b = p->batch;
+    if (!b) return;
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    for (int i = 0; i < 2; ++i) {
+        if (b->stage_ev[i]) cudaEventDestroy(b->stage_ev[i]);
+        if (b->h_stage[i]) cudaFreeHost(b->h_stage[i]);
+    }
+    if (b->d_desc) cudaFree(b->d_desc);
+    if (b->d_start) cudaFree(b->d_start);
+    if (b->d_counter) cudaFree(b->d_counter);
+    delete b;
     p->batch = nullptr;
 }
 
@@ -50,15 +485,55 @@ extern "C" ecc_status ecc_compute_batch(ecc_plan_t p, int32_t n, const ecc_image
     }
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     p->last_launches = 0;
+
+    if (p->d.flags & ECC_FLAG_BATCH_PER_IMAGE) {
+        for (int32_t i = 0; i < n; ++i) {
+            const Geom &g = geoms[i];
+            HistDst h{p->acc + (size_t)i * p->nbins, p->d.lo, p->nbins};
+            cudaError_t e = launch_stencil(p, g, 0, g.ndim == 3 ? g.nz : g.ny, h, s);
+            if (e != cudaSuccess) return cuda_fail(e, "ecc_compute_batch: stencil launch");
+        }
+        cudaError_t e = launch_scan(p->acc, reinterpret_cast<long long *>(d_ecc), nullptr, n, p->nbins,
+                                    p->scan_ws(), p->status, s);
+        ++p->last_launches;
+        if (e != cudaSuccess) return cuda_fail(e, "ecc_compute_batch: scan launch");
+        return ECC_OK;
+    }
+
+    ecc_status st = ensure_batch(p);
+    if (st != ECC_OK) return st;
+    BatchState *b = p->batch;
+    // the staging buffer used two calls ago must be free before rewriting it
+    const int buf = b->next;
+    b->next ^= 1;
+    cudaError_t e = cudaEventSynchronize(b->stage_ev[buf]);
+    if (e != cudaSuccess) return cuda_fail(e, "ecc_compute_batch: staging wait");
+    BatchHeader *hh = reinterpret_cast<BatchHeader *>(b->h_stage[buf]);
+    BatchImage *hi = reinterpret_cast<BatchImage *>(b->h_stage[buf] + sizeof(BatchHeader));
+    hh->n = n;
     for (int32_t i = 0; i < n; ++i) {
         const Geom &g = geoms[i];
-        HistDst h{p->acc + (size_t)i * p->nbins, p->d.lo, p->nbins};
-        cudaError_t e = launch_stencil(p, g, 0, g.ndim == 3 ? g.nz : g.ny, h, s);
-        if (e != cudaSuccess) return cuda_fail(e, "ecc_compute_batch: stencil launch");
+        hi[i] = BatchImage{g.data, g.nx, g.ny, g.nz, g.pitch_y, g.pitch_z, g.ndim, g.esize};
     }
-    cudaError_t e = launch_scan(p->acc, reinterpret_cast<long long *>(d_ecc), nullptr, n, p->nbins,
-                                p->scan_ws(), p->status, s);
-    ++p->last_launches;
-    if (e != cudaSuccess) return cuda_fail(e, "ecc_compute_batch: scan launch");
+    const size_t bytes = sizeof(BatchHeader) + sizeof(BatchImage) * (size_t)n;
+    cudaMemcpy3DParms cp{};
+    cp.srcPtr = make_cudaPitchedPtr(b->h_stage[buf], bytes, bytes, 1);
+    cp.dstPtr = make_cudaPitchedPtr(b->d_desc, bytes, bytes, 1);
+    cp.extent = make_cudaExtent(bytes, 1, 1);
+    cp.kind = cudaMemcpyHostToDevice;
+    e = cudaGraphExecMemcpyNodeSetParams(b->exec, b->copy_node, &cp);
+    if (e == cudaSuccess) {
+        b->scan.ecc = reinterpret_cast<long long *>(d_ecc);
+        cudaKernelNodeParams kp{};
+        kp.func = const_cast<void *>(scan_kernel_entry());
+        kp.gridDim = dim3(b->scan_grid);
+        kp.blockDim = dim3(kScanThreads);
+        kp.kernelParams = b->scan_argv;
+        e = cudaGraphExecKernelNodeSetParams(b->exec, b->scan_node, &kp);
+    }
+    if (e == cudaSuccess) e = cudaGraphLaunch(b->exec, s);
+    if (e == cudaSuccess) e = cudaEventRecord(b->stage_ev[buf], s);
+    if (e != cudaSuccess) return cuda_fail(e, "ecc_compute_batch: graph launch");
+    p->last_launches = 3;  // work list, persistent kernel, scan
     return ECC_OK;
 }

@@ -38,6 +38,7 @@
 
 #include "ecc_bitslice.cuh"
 #include "ecc_internal.h"
+#include "ecc_walk.cuh"
 
 namespace ecc {
 namespace {
@@ -127,42 +128,6 @@ __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, i
         : "memory");
 }
 
-__device__ __forceinline__ uint32_t shfl_from_next(uint32_t v) { return __shfl_down_sync(0xffffffffu, v, 1); }
-__device__ __forceinline__ uint32_t shfl_from_prev(uint32_t v) { return __shfl_up_sync(0xffffffffu, v, 1); }
-
-// r[x] = m[x + dx]
-template <int DX>
-__device__ __forceinline__ uint32_t at_offset(uint32_t m)
-{
-    return DX > 0 ? (m >> 1) : (DX < 0 ? (m << 1) : m);
-}
-
-// win mask from a comparison and the neighbour's existence: in the vertex
-// complex a missing neighbour means the cell does not exist (no win); in the
-// top-cell complex the voxel alone owns it (win) -- the +infinity collar.
-template <bool TOP>
-__device__ __forceinline__ uint32_t with_exist(uint32_t cmp, uint32_t exist)
-{
-    return TOP ? (cmp | ~exist) : (cmp & exist);
-}
-
-// a beats b, b later in linear order (ties go to a).
-template <int K, bool TOP>
-__device__ __forceinline__ uint32_t beats_later(const uint32_t *a, const uint32_t *b)
-{
-    return TOP ? bs::ge<K>(b, a) : bs::ge<K>(a, b);
-}
-
-template <int K>
-__device__ __forceinline__ void shifted(const uint32_t *a, uint32_t *p, uint32_t *m)
-{
-#pragma unroll
-    for (int k = 0; k < K; ++k) {
-        p[k] = a[k] >> 1;  // bit x holds voxel x+1
-        m[k] = a[k] << 1;  // bit x holds voxel x-1
-    }
-}
-
 // Read this lane's 32-voxel window from the staged tile row and transpose it.
 template <typename T>
 __device__ __forceinline__ void load_window(const unsigned char *row, int off, uint32_t *planes)
@@ -200,36 +165,49 @@ __device__ __forceinline__ void load_window(const unsigned char *row, int off, u
         bs::transpose_u16(r, planes);
 }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// NW compute warps and one producer warp.  Stage s of the ring has a "full"
+// barrier (the TMA's transaction count) and an "empty" barrier (one arrival
+// per compute warp once it has copied its window out of the stage), so the
+// warps never wait for each other, only for data.
 template <typename T, int NW, bool TOP, int HREP>
-__global__ void __launch_bounds__(NW * 32) bs3d_kernel(const __grid_constant__ CUtensorMap tmap, const Bs3dArgs a)
+__global__ void __launch_bounds__((NW + 1) * 32) bs3d_kernel(const __grid_constant__ CUtensorMap tmap,
+                                                             const Bs3dArgs a)
 {
     using C = Cfg<T>;
     constexpr int K = C::K, S = C::S, ES = C::ES;
     constexpr int BWB = box_bytes(NW, ES);
     constexpr int STAGE = 32 * BWB;
-    constexpr int NTH = NW * 32;
+    constexpr int NTH = (NW + 1) * 32;
     constexpr int ALIGN_EL = 16 / ES;
 
     extern __shared__ __align__(128) unsigned char smem[];
     unsigned char *stages = smem;
-    uint64_t *bar = reinterpret_cast<uint64_t *>(smem + S * STAGE);
-    int *hist = reinterpret_cast<int *>(bar + S);
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + S * STAGE);
+    uint64_t *empty = full + S;
+    int *hist = reinterpret_cast<int *>(empty + S);
     __shared__ int s_abort;
+    __shared__ long long s_consumed[NW];
+    __shared__ long long s_issued;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (a.smem_hist)
         for (int i = tid; i < HREP * a.h.nbins; i += NTH) hist[i] = 0;
     if (tid == 0) {
-        for (int s = 0; s < S; ++s) mbar_init(&bar[s], 1);
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], NW);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         s_abort = 0;
+        s_issued = 0;
     }
     __syncthreads();
-    int *my_hist = hist + (warp % HREP) * a.h.nbins;
 
-    // -------------------------------------------------------------- producer
-    // Steps are the tile planes of this CTA's items in order; item i covers
-    // output planes [zb, ze) and loads planes zb-1 .. ze.
     auto decode = [&](int item, int &xt, int &yt, int64_t &zb, int64_t &ze) {
         xt = item % a.ntx;
         const int r = item / a.ntx;
@@ -238,224 +216,125 @@ __global__ void __launch_bounds__(NW * 32) bs3d_kernel(const __grid_constant__ C
         zb = a.z_begin + (int64_t)zc * a.zchunk;
         ze = zb + a.zchunk < a.z_end ? zb + a.zchunk : a.z_end;
     };
-    int p_item = blockIdx.x;
-    int64_t p_j = 0, p_g = 0;
-    auto issue_one = [&]() {
-        if (p_item >= a.nitems) return;
-        int xt, yt;
-        int64_t zb, ze;
-        decode(p_item, xt, yt, zb, ze);
-        const int64_t X0 = (int64_t)xt * (kOut * NW);
-        const int64_t xm = X0 - 1;
-        const int64_t bx = (xm >= 0 ? xm / ALIGN_EL : -((-xm + ALIGN_EL - 1) / ALIGN_EL)) * ALIGN_EL;
-        const int64_t Y0 = (int64_t)yt * kOut - 1;
-        const int64_t z = zb - 1 + p_j;
-        const int s = (int)(p_g % S);
-        mbar_expect_tx(&bar[s], STAGE);
-        tma_load_3d(stages + (size_t)s * STAGE, &tmap, (int)bx, (int)Y0, (int)z, &bar[s]);
-        ++p_g;
-        if (++p_j == ze - zb + 2) {
-            p_j = 0;
-            p_item += gridDim.x;
-        }
-    };
-    if (tid == 0)
-        for (int i = 0; i < S; ++i) issue_one();
-
-    // -------------------------------------------------------------- consumer
-    int64_t g = 0;
-    bool aborted = false;
-    auto end_step = [&]() {
-        __syncthreads();  // every warp is done with step g-1's stage
-        if (s_abort) aborted = true;
-        if (tid == 0 && g >= 1 && !aborted) issue_one();
-        ++g;
-    };
-    auto wait_stage = [&]() -> const unsigned char * {
-        const int s = (int)(g % S);
-        if (!mbar_wait(&bar[s], (uint32_t)((g / S) & 1))) {
-            if (lane == 0) {
-                atomicOr(a.status, DEV_TIMEOUT);
-                atomicExch(&s_abort, 1);
-            }
-            return nullptr;
-        }
-        return stages + (size_t)s * STAGE;
+    auto box_x = [&](int xt) -> int64_t {
+        const int64_t xm = (int64_t)xt * (kOut * NW) - 1;
+        return (xm >= 0 ? xm / ALIGN_EL : -((-xm + ALIGN_EL - 1) / ALIGN_EL)) * ALIGN_EL;
     };
 
-    for (int item = blockIdx.x; item < a.nitems && !aborted; item += gridDim.x) {
-        int xt, yt;
-        int64_t zb, ze;
-        decode(item, xt, yt, zb, ze);
-        const int64_t X0 = (int64_t)xt * (kOut * NW);
-        const int64_t xm = X0 - 1;
-        const int64_t bx = (xm >= 0 ? xm / ALIGN_EL : -((-xm + ALIGN_EL - 1) / ALIGN_EL)) * ALIGN_EL;
-        const int64_t y = (int64_t)yt * kOut - 1 + lane;
-        const int64_t xw = X0 + kOut * warp - 1;  // voxel of window bit 0
-        const int off = (int)((xw - bx) * ES);
-
-        // x existence of each window bit's voxel, and of its +-1 neighbours
-        uint32_t xex = 0;
-        {
-            const int64_t lo_i = -xw, hi_i = a.nx - xw;  // bits i with 0 <= xw+i < nx
-            const int l = lo_i < 0 ? 0 : (lo_i > 32 ? 32 : (int)lo_i);
-            const int h = hi_i < 0 ? 0 : (hi_i > 32 ? 32 : (int)hi_i);
-            if (h > l) xex = (h - l == 32 ? 0xffffffffu : (((1u << (h - l)) - 1u) << l));
-        }
-        const uint32_t ex_p = xex >> 1, ex_m = xex << 1;  // neighbour at x+1 / x-1 exists
-        const uint32_t ex_x[3] = {ex_m, 0xffffffffu, ex_p};
-        const bool lane_out = lane >= 1 && lane <= kOut && y < a.ny;
-        const uint32_t out_x = xex & 0x7ffffffeu;
-        const uint32_t ey_m = (y - 1 >= 0 && y - 1 < a.ny) ? 0xffffffffu : 0u;
-        const uint32_t ey_p = (y + 1 >= 0 && y + 1 < a.ny) ? 0xffffffffu : 0u;
-        const uint32_t ey[3] = {ey_m, 0xffffffffu, ey_p};
-
-        uint32_t A[K], Au[K];
-        uint32_t wx[3] = {0, 0, 0}, wyp[3] = {0, 0, 0}, wym[3] = {0, 0, 0}, Wm[3][3] = {};
-        // prologue: plane zb-1
-        {
-            const unsigned char *st = wait_stage();
-            if (st) {
-                load_window<T>(st + lane * BWB, off, A);
-#pragma unroll
-                for (int k = 0; k < K; ++k) Au[k] = shfl_from_next(A[k]);
-            }
-            end_step();
-        }
-        for (int64_t z1 = zb; z1 <= ze && !aborted; ++z1) {
-            const unsigned char *st = wait_stage();
-            if (st) {
-                const unsigned char *st_prev = stages + (size_t)((g - 1) % S) * STAGE;
-                uint32_t B[K], Bu[K];
-                load_window<T>(st + lane * BWB, off, B);
-#pragma unroll
-                for (int k = 0; k < K; ++k) Bu[k] = shfl_from_next(B[k]);
-
-                // inter-plane comparisons, (z, .) earlier than (z+1, .)
-                uint32_t H0[3], Hp[3], Kp[3];
-                {
-                    uint32_t Ap[K], Am[K];
-                    shifted<K>(A, Ap, Am);
-                    H0[0] = beats_later<K, TOP>(Ap, B);  // [x] = A[x+1] vs B[x]
-                    H0[1] = beats_later<K, TOP>(A, B);
-                    H0[2] = beats_later<K, TOP>(Am, B);  // [x] = A[x-1] vs B[x]
-                    Hp[0] = beats_later<K, TOP>(Ap, Bu);
-                    Hp[1] = beats_later<K, TOP>(A, Bu);
-                    Hp[2] = beats_later<K, TOP>(Am, Bu);
-                    uint32_t Aup[K], Aum[K];
-                    shifted<K>(Au, Aup, Aum);
-                    Kp[0] = beats_later<K, TOP>(Aup, B);
-                    Kp[1] = beats_later<K, TOP>(Au, B);
-                    Kp[2] = beats_later<K, TOP>(Aum, B);
-                }
-                uint32_t Hp_dn[3], Kp_dn[3];
-#pragma unroll
-                for (int d = 0; d < 3; ++d) {
-                    Hp_dn[d] = shfl_from_prev(Hp[d]);
-                    Kp_dn[d] = shfl_from_prev(Kp[d]);
-                }
-                // in-plane comparisons of plane z+1
-                uint32_t E, F[3], F_dn[3];
-                {
-                    uint32_t Bp[K], Bm[K];
-                    shifted<K>(B, Bp, Bm);
-                    E = beats_later<K, TOP>(Bm, B);       // [x] = B[x-1] vs B[x]
-                    F[0] = beats_later<K, TOP>(Bp, Bu);   // [x] = B[x+1] vs Bu[x]
-                    F[1] = beats_later<K, TOP>(B, Bu);
-                    F[2] = beats_later<K, TOP>(Bm, Bu);   // [x] = B[x-1] vs Bu[x]
-                }
-#pragma unroll
-                for (int d = 0; d < 3; ++d) F_dn[d] = shfl_from_prev(F[d]);
-
-                const int64_t z = z1 - 1;
-                const uint32_t ez_p = z1 < a.nz ? 0xffffffffu : 0u;   // plane z+1 exists
-                const uint32_t ez_m1 = z >= 0 ? 0xffffffffu : 0u;     // plane z exists (for z+1's wins)
-
-                // wins of (z, y, x) over plane z+1: [dy][dx]
-                uint32_t Wp[3][3];
-                Wp[1][0] = at_offset<-1>(H0[0]);
-                Wp[1][1] = H0[1];
-                Wp[1][2] = at_offset<+1>(H0[2]);
-                Wp[2][0] = at_offset<-1>(Hp[0]);
-                Wp[2][1] = Hp[1];
-                Wp[2][2] = at_offset<+1>(Hp[2]);
-                Wp[0][0] = at_offset<-1>(Kp_dn[0]);
-                Wp[0][1] = Kp_dn[1];
-                Wp[0][2] = at_offset<+1>(Kp_dn[2]);
-#pragma unroll
-                for (int dy = 0; dy < 3; ++dy)
-#pragma unroll
-                    for (int dx = 0; dx < 3; ++dx) Wp[dy][dx] = with_exist<TOP>(Wp[dy][dx], ez_p & ey[dy] & ex_x[dx]);
-
-                if (z >= zb && lane_out) {
-                    uint32_t w[3][3][3];
-#pragma unroll
-                    for (int dy = 0; dy < 3; ++dy)
-#pragma unroll
-                        for (int dx = 0; dx < 3; ++dx) {
-                            w[0][dy][dx] = Wm[dy][dx];
-                            w[2][dy][dx] = Wp[dy][dx];
-                        }
-                    w[1][1][0] = wx[0];
-                    w[1][1][2] = wx[2];
-                    w[1][1][1] = 0;
-#pragma unroll
-                    for (int dx = 0; dx < 3; ++dx) {
-                        w[1][0][dx] = wym[dx];
-                        w[1][2][dx] = wyp[dx];
+    if (warp == NW) {
+        // ------------------------------------------------------ producer warp
+        if (lane == 0) {
+            int64_t g = 0;
+            for (int item = blockIdx.x; item < a.nitems; item += gridDim.x) {
+                int xt, yt;
+                int64_t zb, ze;
+                decode(item, xt, yt, zb, ze);
+                const int bx = (int)box_x(xt);
+                const int y0 = yt * kOut - 1;
+                for (int64_t z = zb - 1; z <= ze; ++z, ++g) {
+                    const int s = (int)(g % S);
+                    if (g >= S && !mbar_wait(&empty[s], (uint32_t)(((g / S) - 1) & 1))) {
+                        atomicOr(a.status, DEV_TIMEOUT);
+                        atomicExch(&s_abort, 1);
+                        break;
                     }
-                    uint32_t Sq[4], Nc[4];
-                    uint32_t m = bs::kappa3d(w, Sq, Nc) & out_x;
-                    const unsigned char *vrow = st_prev + lane * BWB + off;
-                    while (m) {
-                        const int i = __ffs(m) - 1;
-                        m &= m - 1;
-                        int kap = 1 + bs::bits_at<4>(Sq, i) - bs::bits_at<4>(Nc, i);
-                        if (TOP) kap = -kap;  // (-1)^d, d = 3
-                        const int v = ES == 1 ? (int)vrow[i] : (int)*reinterpret_cast<const unsigned short *>(vrow + 2 * i);
-                        const int bin = v - a.h.lo;
-                        if (a.range_check && (unsigned)bin >= (unsigned)a.h.nbins) {
-                            atomicOr(a.status, DEV_RANGE);
-                            continue;
-                        }
-                        if (a.smem_hist)
-                            atomicAdd(&my_hist[bin], kap);
-                        else
-                            atomicAdd(a.h.acc + bin, (unsigned long long)(long long)kap);
-                    }
+                    if (*(volatile int *)&s_abort) break;
+                    mbar_expect_tx(&full[s], STAGE);
+                    tma_load_3d(stages + (size_t)s * STAGE, &tmap, bx, y0, (int)z, &full[s]);
+                    s_issued = g + 1;
                 }
-
-                // wins of (z+1, y, x) over plane z, kept for the next step
-#pragma unroll
-                for (int dx = 0; dx < 3; ++dx) {
-                    // neighbour (z, y+dy, x+dx) is earlier: win = not (it beats us)
-                    Wm[1][dx] = with_exist<TOP>(~H0[2 - dx], ez_m1 & ey[1] & ex_x[dx]);
-                    Wm[2][dx] = with_exist<TOP>(~Kp[2 - dx], ez_m1 & ey[2] & ex_x[dx]);
-                    Wm[0][dx] = with_exist<TOP>(~Hp_dn[2 - dx], ez_m1 & ey[0] & ex_x[dx]);
-                }
-                // in-plane wins of (z+1, y, x)
-                wx[2] = with_exist<TOP>(at_offset<+1>(E), ex_p);
-                wx[0] = with_exist<TOP>(~E, ex_m);
-                wyp[0] = with_exist<TOP>(at_offset<-1>(F[0]), ey_p & ex_m);
-                wyp[1] = with_exist<TOP>(F[1], ey_p);
-                wyp[2] = with_exist<TOP>(at_offset<+1>(F[2]), ey_p & ex_p);
-#pragma unroll
-                for (int dx = 0; dx < 3; ++dx) wym[dx] = with_exist<TOP>(~F_dn[2 - dx], ey_m & ex_x[dx]);
-#pragma unroll
-                for (int k = 0; k < K; ++k) {
-                    A[k] = B[k];
-                    Au[k] = Bu[k];
-                }
+                if (*(volatile int *)&s_abort) break;
             }
-            end_step();
         }
+    } else {
+        // ------------------------------------------------------ compute warps
+        int *my_hist = hist + (warp % HREP) * a.h.nbins;
+        int64_t g = 0;
+        bool ok = true;
+        auto fetch = [&](walk::Rows3<K> &r) {
+            // wait for step g's stage, copy this lane's window, release the stage
+            const int s = (int)(g % S);
+            if (ok && !mbar_wait(&full[s], (uint32_t)((g / S) & 1))) {
+                if (lane == 0) {
+                    atomicOr(a.status, DEV_TIMEOUT);
+                    atomicExch(&s_abort, 1);
+                }
+                ok = false;
+            }
+            if (ok) {
+                load_window<T>(stages + (size_t)s * STAGE + lane * BWB, r.off, r.P);
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&empty[s]);
+            }
+            ++g;
+            walk::complete_rows<K>(r);
+        };
+        for (int item = blockIdx.x; item < a.nitems && ok; item += gridDim.x) {
+            int xt, yt;
+            int64_t zb, ze;
+            decode(item, xt, yt, zb, ze);
+            const int64_t X0 = (int64_t)xt * (kOut * NW);
+            const int64_t bx = box_x(xt);
+            const int64_t y0 = (int64_t)yt * kOut - 1;
+            const int64_t y = y0 + lane;
+            const int64_t xw = X0 + kOut * warp - 1;  // voxel of window bit 0
+            const int off = (int)((xw - bx) * ES);
+            const uint32_t xex = walk::x_exist_mask(xw, a.nx);
+            const bool lane_out = lane >= 1 && lane <= kOut && y < a.ny;
+            const uint32_t out_x = lane_out ? (xex & 0x7ffffffeu) : 0u;
+            // interior: every voxel of the window and of the 30 output rows has
+            // all its x and y neighbours
+            const bool inner_xy = xw >= 0 && xw + 32 <= a.nx && y0 >= 0 && y0 + 31 < a.ny;
+            walk::Walk3d<K, TOP> wk;
+            wk.begin(xex, y - 1 >= 0 && y - 1 < a.ny, y + 1 >= 0 && y + 1 < a.ny);
+            auto emit = [&](uint32_t m, const uint32_t *Sq, const uint32_t *Nc, const uint32_t *A) {
+                while (m) {
+                    const int i = __ffs(m) - 1;
+                    m &= m - 1;
+                    int kap = 1 + bs::bits_at<4>(Sq, i) - bs::bits_at<4>(Nc, i);
+                    if (TOP) kap = -kap;  // (-1)^d, d = 3
+                    const int bin = bs::bits_at<K>(A, i) - a.h.lo;
+                    if (a.range_check && (unsigned)bin >= (unsigned)a.h.nbins) {
+                        atomicOr(a.status, DEV_RANGE);
+                        continue;
+                    }
+                    if (a.smem_hist)
+                        atomicAdd(&my_hist[bin], kap);
+                    else
+                        atomicAdd(a.h.acc + bin, (unsigned long long)(long long)kap);
+                }
+            };
+            walk::Rows3<K> r0, r1;
+            r0.off = r1.off = off;
+            fetch(r0);  // plane zb-1
+            int64_t z1 = zb;
+            auto advance = [&](const walk::Rows3<K> &cur, const walk::Rows3<K> &nxt) {
+                const bool zp = z1 < a.nz, zok = z1 - 1 >= 0;
+                const bool emit_z = z1 - 1 >= zb;
+                if (inner_xy && zp && zok)
+                    wk.template step<false>(cur, nxt, zp, zok, emit_z, out_x, emit);
+                else
+                    wk.template step<true>(cur, nxt, zp, zok, emit_z, out_x, emit);
+                ++z1;
+            };
+            while (ok) {
+                fetch(r1);
+                advance(r0, r1);
+                if (z1 > ze || !ok) break;
+                fetch(r0);
+                advance(r1, r0);
+                if (z1 > ze) break;
+            }
+        }
+        if (lane == 0) s_consumed[warp] = g;
     }
 
-    if (aborted) {
-        // wait (bounded) for the copies still in flight before leaving
-        if (tid == 0)
-            for (int64_t q = g; q < p_g; ++q) mbar_wait(&bar[q % S], (uint32_t)((q / S) & 1));
-        __syncthreads();
+    __syncthreads();
+    if (s_abort && tid == 0) {
+        // wait (bounded) for copies still in flight before leaving
+        long long lo = s_issued;
+        for (int w = 0; w < NW; ++w) lo = s_consumed[w] < lo ? s_consumed[w] : lo;
+        for (long long q = lo; q < s_issued; ++q) mbar_wait(&full[q % S], (uint32_t)((q / S) & 1));
     }
     __syncthreads();
     if (a.smem_hist)
@@ -491,36 +370,6 @@ struct Bs2dArgs {
 
 constexpr int kWarps2d = 4;
 
-template <typename T>
-__device__ __forceinline__ void load_row_words(const unsigned char *row, int64_t row_bytes, int64_t first_byte,
-                                               uint32_t *w)
-{
-    // words covering bytes [first_byte, first_byte + 32*ES) of the row, from
-    // the 4-byte aligned address at or below it; 0 where no row byte lies
-    using C = Cfg<T>;
-    const uintptr_t start = reinterpret_cast<uintptr_t>(row) + first_byte;
-    const uintptr_t a0 = start & ~uintptr_t(3);
-    const uintptr_t lo = reinterpret_cast<uintptr_t>(row), hi = lo + row_bytes;
-#pragma unroll
-    for (int i = 0; i <= C::WORDS; ++i) {
-        const uintptr_t ad = a0 + 4 * i;
-        w[i] = (ad + 4 > lo && ad < hi) ? __ldg(reinterpret_cast<const uint32_t *>(ad)) : 0u;
-    }
-}
-
-template <typename T>
-__device__ __forceinline__ void window_from_words(const uint32_t *w, int sh, uint32_t *planes)
-{
-    using C = Cfg<T>;
-    uint32_t raw[C::WORDS];
-#pragma unroll
-    for (int i = 0; i < C::WORDS; ++i) raw[i] = __funnelshift_r(w[i], w[i + 1], sh);
-    if (C::ES == 1)
-        bs::transpose_u8(raw, planes);
-    else
-        bs::transpose_u16(raw, planes);
-}
-
 template <typename T, bool TOP, int HREP>
 __global__ void __launch_bounds__(kWarps2d * 32) bs2d_kernel(const Bs2dArgs a)
 {
@@ -540,94 +389,45 @@ __global__ void __launch_bounds__(kWarps2d * 32) bs2d_kernel(const Bs2dArgs a)
         const int64_t ye = yb + a.ychunk < a.y_end ? yb + a.ychunk : a.y_end;
         const int64_t xw = (int64_t)xt * (32 * kOut) + kOut * lane - 1;  // voxel of window bit 0
         const int64_t first = xw * ES;                                    // may be negative at x = 0
-        uint32_t xex = 0;
-        {
-            const int64_t lo_i = -xw, hi_i = a.nx - xw;
-            const int l = lo_i < 0 ? 0 : (lo_i > 32 ? 32 : (int)lo_i);
-            const int h = hi_i < 0 ? 0 : (hi_i > 32 ? 32 : (int)hi_i);
-            if (h > l) xex = (h - l == 32 ? 0xffffffffu : (((1u << (h - l)) - 1u) << l));
-        }
-        const uint32_t ex_p = xex >> 1, ex_m = xex << 1;
-        const uint32_t ex_x[3] = {ex_m, 0xffffffffu, ex_p};
+        const uint32_t xex = walk::x_exist_mask(xw, a.nx);
         const uint32_t out_x = xex & 0x7ffffffeu;
-        if (!xex) continue;  // lane past the right edge: nothing to read or emit
-
         // the byte shift of the window inside its aligned words depends on the
         // row's address (pitches need not be multiples of 4)
-        auto fetch = [&](int64_t yy, uint32_t *w, int &sh) {
-            if (yy < 0 || yy >= a.ny) {
+        auto fetch = [&](int64_t yy, uint32_t *w) -> int {
+            if (yy < 0 || yy >= a.ny || !xex) {
 #pragma unroll
-                for (int i = 0; i <= C::WORDS; ++i) w[i] = 0;
-                sh = 0;
-            } else {
-                const unsigned char *row = a.data + yy * a.pitch;
-                sh = (int)((reinterpret_cast<uintptr_t>(row) + (uintptr_t)first) & 3u) * 8;
-                load_row_words<T>(row, row_bytes, first, w);
+                for (int i = 0; i <= K; ++i) w[i] = 0;
+                return 0;
+            }
+            return walk::load_row_words<K>(a.data + yy * a.pitch, row_bytes, first, w);
+        };
+        auto emit = [&](uint32_t m, const uint32_t *Q, const uint32_t *F, const uint32_t *A) {
+            while (m) {
+                const int i = __ffs(m) - 1;
+                m &= m - 1;
+                const int kap = 1 + bs::bits_at<3>(Q, i) - bs::bits_at<3>(F, i);  // (-1)^2 = +1
+                const int bin = bs::bits_at<K>(A, i) - a.h.lo;
+                if (a.range_check && (unsigned)bin >= (unsigned)a.h.nbins) {
+                    atomicOr(a.status, DEV_RANGE);
+                    continue;
+                }
+                if (a.smem_hist)
+                    atomicAdd(&my_hist[bin], kap);
+                else
+                    atomicAdd(a.h.acc + bin, (unsigned long long)(long long)kap);
             }
         };
-        uint32_t wnext[C::WORDS + 1], A[K];
-        int sh_next;
-        {
-            uint32_t w0[C::WORDS + 1];
-            int sh0;
-            fetch(yb - 1, w0, sh0);
-            window_from_words<T>(w0, sh0, A);
-        }
-        fetch(yb, wnext, sh_next);
-        uint32_t wx[3] = {0, 0, 0}, wym[3] = {0, 0, 0};
+        uint32_t wn[K + 1], P[K];
+        int sh = fetch(yb - 1, wn);
+        walk::planes_from_words<K>(wn, sh, P);
+        walk::Walk2d<K, TOP> wk;
+        wk.begin(P, xex);
+        sh = fetch(yb, wn);
         for (int64_t y1 = yb; y1 <= ye; ++y1) {
             uint32_t B[K];
-            window_from_words<T>(wnext, sh_next, B);
-            if (y1 + 1 <= ye) fetch(y1 + 1, wnext, sh_next);  // prefetch the next row
-            uint32_t H[3], E;
-            {
-                uint32_t Ap[K], Am[K], Bp[K], Bm[K];
-                shifted<K>(A, Ap, Am);
-                shifted<K>(B, Bp, Bm);
-                H[0] = beats_later<K, TOP>(Ap, B);  // [x] = A[x+1] vs B[x]
-                H[1] = beats_later<K, TOP>(A, B);
-                H[2] = beats_later<K, TOP>(Am, B);  // [x] = A[x-1] vs B[x]
-                E = beats_later<K, TOP>(Bm, B);     // [x] = B[x-1] vs B[x]
-            }
-            const int64_t y = y1 - 1;
-            const uint32_t ey_p = y1 < a.ny ? 0xffffffffu : 0u;
-            const uint32_t ey_m1 = y >= 0 ? 0xffffffffu : 0u;
-            if (y >= yb) {
-                uint32_t w[3][3];
-                w[0][0] = wym[0];
-                w[0][1] = wym[1];
-                w[0][2] = wym[2];
-                w[1][0] = wx[0];
-                w[1][1] = 0;
-                w[1][2] = wx[2];
-                w[2][0] = with_exist<TOP>(at_offset<-1>(H[0]), ey_p & ex_m);
-                w[2][1] = with_exist<TOP>(H[1], ey_p);
-                w[2][2] = with_exist<TOP>(at_offset<+1>(H[2]), ey_p & ex_p);
-                uint32_t F[3], Q[3];
-                uint32_t m = bs::kappa2d(w, F, Q) & out_x;
-                while (m) {
-                    const int i = __ffs(m) - 1;
-                    m &= m - 1;
-                    const int kap = 1 + bs::bits_at<3>(Q, i) - bs::bits_at<3>(F, i);  // (-1)^2 = +1
-                    const int v = bs::bits_at<K>(A, i);  // the voxel's gray level from its bit planes
-                    const int bin = v - a.h.lo;
-                    if (a.range_check && (unsigned)bin >= (unsigned)a.h.nbins) {
-                        atomicOr(a.status, DEV_RANGE);
-                        continue;
-                    }
-                    if (a.smem_hist)
-                        atomicAdd(&my_hist[bin], kap);
-                    else
-                        atomicAdd(a.h.acc + bin, (unsigned long long)(long long)kap);
-                }
-            }
-            // wins of row y+1 for the next step
-#pragma unroll
-            for (int dx = 0; dx < 3; ++dx) wym[dx] = with_exist<TOP>(~H[2 - dx], ey_m1 & ex_x[dx]);
-            wx[2] = with_exist<TOP>(at_offset<+1>(E), ex_p);
-            wx[0] = with_exist<TOP>(~E, ex_m);
-#pragma unroll
-            for (int k = 0; k < K; ++k) A[k] = B[k];
+            walk::planes_from_words<K>(wn, sh, B);
+            if (y1 + 1 <= ye) sh = fetch(y1 + 1, wn);  // prefetch the next row
+            wk.step(B, y1 < a.ny, y1 - 1 >= 0, y1 - 1 >= yb, out_x, emit);
         }
     }
     __syncthreads();
@@ -740,7 +540,7 @@ cudaError_t launch_t(const Geom &g, int64_t zb, int64_t ze, const HistDst &h, bo
     a.h = h;
     a.range_check = range_check;
     a.status = status;
-    const size_t stage_bytes = (size_t)C::S * 32 * BWB + (size_t)C::S * 8;
+    const size_t stage_bytes = (size_t)C::S * 32 * BWB + (size_t)C::S * 16;
     a.smem_hist = (size_t)HREP * h.nbins * 4 + stage_bytes <= 160 * 1024;
     const size_t smem = stage_bytes + (a.smem_hist ? (size_t)HREP * h.nbins * 4 : 0);
     auto kern = bs3d_kernel<T, NW, TOP, HREP>;
@@ -756,7 +556,7 @@ cudaError_t launch_t(const Geom &g, int64_t zb, int64_t ze, const HistDst &h, bo
         attr_smem = smem;
     }
     if (occ_smem != smem || per_sm == 0) {
-        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NW * 32, smem);
+        cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, (NW + 1) * 32, smem);
         if (e != cudaSuccess) return e;
         occ_smem = smem;
     }
@@ -774,7 +574,7 @@ cudaError_t launch_t(const Geom &g, int64_t zb, int64_t ze, const HistDst &h, bo
     if (items > 2147483647) return cudaErrorNotSupported;
     a.nitems = (int32_t)items;
     const int64_t ctas = items < ctas_max ? items : ctas_max;
-    kern<<<(unsigned)ctas, NW * 32, smem, s>>>(map, a);
+    kern<<<(unsigned)ctas, (NW + 1) * 32, smem, s>>>(map, a);
     return cudaGetLastError();
 }
 

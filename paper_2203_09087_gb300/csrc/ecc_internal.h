@@ -54,6 +54,25 @@ constexpr int kScanThreads = 256;
 constexpr int kScanItems = 8;
 constexpr int kScanTile = kScanThreads * kScanItems;
 
+// Arguments of the scan kernel.  When n_seg_dev is set, the number of
+// segments is read from device memory (*n_seg_dev) instead of n, so a
+// captured graph can scan a different number of images on every launch;
+// CTAs beyond the data then only take part in the workspace reset.
+struct ScanArgs {
+    unsigned long long *acc;
+    long long *ecc;
+    long long *vcec;
+    int64_t n;
+    int32_t nbins;
+    int32_t ntiles;
+    ScanWs ws;
+    unsigned int *status;
+    const int *n_seg_dev;
+};
+
+// The scan kernel's entry (for graph nodes); grid = scan_tiles(), block = kScanThreads.
+const void *scan_kernel_entry();
+
 // --------------------------------------------------------------- launchers
 
 // One-thread-per-voxel stencil + histogram over the voxels whose outer index

@@ -42,6 +42,8 @@ struct ecc_plan_s {
 
     // tile parameter per (ndim, esize) key chosen by the autotuner
     int tuned[4] = {0, 0, 0, 0};
+    // batch path: rows per 2D tile, planes per 3D tile (0 = default)
+    int tuned_batch[2] = {0, 0};
 
     ecc::BatchState *batch = nullptr;
 

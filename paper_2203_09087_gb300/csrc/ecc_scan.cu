@@ -16,17 +16,6 @@
 namespace ecc {
 namespace {
 
-struct ScanArgs {
-    unsigned long long *acc;
-    long long *ecc;
-    long long *vcec;
-    int64_t n;
-    int32_t nbins;
-    int32_t ntiles;
-    ScanWs ws;
-    unsigned int *status;
-};
-
 __device__ __forceinline__ unsigned long long globaltimer()
 {
     unsigned long long t;
@@ -51,6 +40,7 @@ __global__ void __launch_bounds__(kScanThreads) scan_kernel(ScanArgs a)
     __shared__ int s_last;
 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (a.n_seg_dev) a.n = (int64_t)(*a.n_seg_dev) * a.nbins;
     if (threadIdx.x == 0) s_tile = atomicAdd(a.ws.tile_counter, 1u);
     __syncthreads();
     const int64_t tile = s_tile;
@@ -147,7 +137,9 @@ __global__ void __launch_bounds__(kScanThreads) scan_kernel(ScanArgs a)
             st[tile] = 1;
         }
         long long carry = 0;
-        const bool needs_carry = (tile * kScanTile) % a.nbins != 0;
+        // tiles past the data (a graph launched for more images than this
+        // call has) need nothing from their predecessors
+        const bool needs_carry = (tile * kScanTile) % a.nbins != 0 && tile * kScanTile < a.n;
         if (needs_carry) {
             int64_t j = tile - 1;
             const unsigned long long t0 = globaltimer();
@@ -201,12 +193,12 @@ __global__ void __launch_bounds__(kScanThreads) scan_kernel(ScanArgs a)
     if (threadIdx.x == 0) {
         __threadfence();
         const unsigned int done = atomicAdd(a.ws.done_counter, 1u);
-        s_last = (done == (unsigned)a.ntiles - 1u);
+        s_last = (done == gridDim.x - 1u);
     }
     __syncthreads();
     if (s_last) {
         __threadfence();
-        for (int i = threadIdx.x; i < a.ntiles; i += kScanThreads) a.ws.tile_status[i] = 0;
+        for (int i = threadIdx.x; i < (int)gridDim.x; i += kScanThreads) a.ws.tile_status[i] = 0;
         if (threadIdx.x == 0) {
             *a.ws.tile_counter = 0u;
             *a.ws.done_counter = 0u;
@@ -215,6 +207,8 @@ __global__ void __launch_bounds__(kScanThreads) scan_kernel(ScanArgs a)
 }
 
 }  // namespace
+
+const void *scan_kernel_entry() { return reinterpret_cast<const void *>(scan_kernel); }
 
 int64_t scan_tiles(int64_t n_seg, int32_t nbins)
 {
@@ -236,6 +230,7 @@ cudaError_t launch_scan(unsigned long long *acc, long long *ecc, long long *vcec
     a.ntiles = (int32_t)nt;
     a.ws = ws;
     a.status = status;
+    a.n_seg_dev = nullptr;
     scan_kernel<<<(unsigned)nt, kScanThreads, 0, s>>>(a);
     return cudaGetLastError();
 }

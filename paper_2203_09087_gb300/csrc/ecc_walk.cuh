@@ -1,0 +1,308 @@
+// ecc_walk.cuh -- warp-level walkers of the bit-sliced stencil (device only).
+//
+// A walker holds one warp's sliding state while it walks an image along its
+// slowest axis and, at every step, emits the voxels of the previous row or
+// plane whose signed cell count is nonzero (Sec. 2.3 "Faces introduced by a
+// voxel"; Algorithm 1 regrouped per voxel).  Windows are 32 voxels of one
+// row held as bit planes, overlapping by one voxel on each side, so bits
+// 1..30 are outputs and the +-1 shifts along x stay in the register.
+//
+//   Walk3d: lane l holds row y0-1+l (lanes 0 and 31 are the y halo); the warp
+//           walks planes z.  Each step compares planes z and z+1 (9 pairs per
+//           voxel) and the in-plane pairs of z+1 (4), sharing the pairs with
+//           row y-1 through shuffles, so each neighbour pair is compared once.
+//   Walk2d: lanes hold consecutive windows of one row; the warp walks rows.
+//
+// A voxel's win over a neighbour that precedes it in memory is the negation
+// of that neighbour's win over it (ties go to the lower linear index).
+#pragma once
+
+#include <stdint.h>
+
+#include "ecc_bitslice.cuh"
+
+namespace ecc {
+namespace walk {
+
+__device__ __forceinline__ uint32_t from_next_lane(uint32_t v) { return __shfl_down_sync(0xffffffffu, v, 1); }
+__device__ __forceinline__ uint32_t from_prev_lane(uint32_t v) { return __shfl_up_sync(0xffffffffu, v, 1); }
+
+// One-bit shifts written as multiplies, so they can issue on the FMA pipe
+// (the integer logic of the stencil saturates the ALU pipe): x << 1 = x * 2,
+// x >> 1 = high word of x * 2^31.
+__device__ __forceinline__ uint32_t shl1(uint32_t x) { return x * 2u; }
+__device__ __forceinline__ uint32_t shr1(uint32_t x) { return __umulhi(x, 0x80000000u); }
+
+// r[x] = m[x + dx]
+template <int DX>
+__device__ __forceinline__ uint32_t at_offset(uint32_t m)
+{
+    return DX > 0 ? shr1(m) : (DX < 0 ? shl1(m) : m);
+}
+
+// A comparison turned into a win: in the vertex complex a missing neighbour
+// means the cell does not exist (no win); in the top-cell complex the voxel
+// owns the boundary cell alone (a win) -- the paper's +infinity collar.
+template <bool TOP>
+__device__ __forceinline__ uint32_t with_exist(uint32_t cmp, uint32_t exist)
+{
+    return TOP ? (cmp | ~exist) : (cmp & exist);
+}
+
+// Voxel a beats voxel b that follows it in memory (a wins ties): the max of
+// the two for the vertex complex, the min for the top-cell complex.
+template <int K, bool TOP>
+__device__ __forceinline__ uint32_t beats_later(const uint32_t *a, const uint32_t *b)
+{
+    return TOP ? bs::ge<K>(b, a) : bs::ge<K>(a, b);
+}
+
+template <int K>
+__device__ __forceinline__ void shifted(const uint32_t *a, uint32_t *p, uint32_t *m)
+{
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        p[k] = shr1(a[k]);  // bit x holds voxel x+1
+        m[k] = shl1(a[k]);  // bit x holds voxel x-1
+    }
+}
+
+// Bits i of a window starting at voxel xw whose voxel lies in [0, nx).
+__device__ __forceinline__ uint32_t x_exist_mask(int64_t xw, int64_t nx)
+{
+    const int64_t lo_i = -xw, hi_i = nx - xw;
+    const int l = lo_i < 0 ? 0 : (lo_i > 32 ? 32 : (int)lo_i);
+    const int h = hi_i < 0 ? 0 : (hi_i > 32 ? 32 : (int)hi_i);
+    if (h <= l) return 0u;
+    return h - l == 32 ? 0xffffffffu : (((1u << (h - l)) - 1u) << l);
+}
+
+// Aligned 32-bit words covering bytes [first, first + 4*NW) of a row of
+// row_bytes bytes, from the aligned address at or below it; a word that holds
+// no byte of the row is not read (0 instead), so no access leaves the row's
+// 4-byte-aligned extent.  Returns the bit shift of the window in the words.
+template <int NW>
+__device__ __forceinline__ int load_row_words(const unsigned char *row, int64_t row_bytes, int64_t first, uint32_t *w)
+{
+    const uintptr_t start = reinterpret_cast<uintptr_t>(row) + (uintptr_t)first;
+    const uintptr_t a0 = start & ~uintptr_t(3);
+    const uintptr_t lo = reinterpret_cast<uintptr_t>(row), hi = lo + (uintptr_t)row_bytes;
+#pragma unroll
+    for (int i = 0; i <= NW; ++i) {
+        const uintptr_t ad = a0 + 4 * i;
+        w[i] = (ad + 4 > lo && ad < hi) ? __ldg(reinterpret_cast<const uint32_t *>(ad)) : 0u;
+    }
+    return (int)(start & 3u) * 8;
+}
+
+// Bit planes of the window held in aligned words w shifted by sh bits.
+template <int K>
+__device__ __forceinline__ void planes_from_words(const uint32_t *w, int sh, uint32_t *planes)
+{
+    constexpr int NW = K;  // 32 voxels of K bits = K words
+    uint32_t raw[NW];
+#pragma unroll
+    for (int i = 0; i < NW; ++i) raw[i] = __funnelshift_r(w[i], w[i + 1], sh);
+    if (K == 8)
+        bs::transpose_u8(raw, planes);
+    else
+        bs::transpose_u16(raw, planes);
+}
+
+// ------------------------------------------------------------------ 3D
+
+// One plane's part of a lane: row y as planes P, row y+1 (the next lane's P)
+// as U, and row y shifted by one voxel each way (Pp[x] = P[x+1], Pm[x] = P[x-1]).
+template <int K>
+struct Rows3 {
+    uint32_t P[K], U[K], Pp[K], Pm[K];
+    int off;  // loader bookkeeping (byte offset of the window in a staged row)
+};
+
+// Fill U and the shifts of a freshly loaded P.  Warp-collective.
+template <int K>
+__device__ __forceinline__ void complete_rows(Rows3<K> &r)
+{
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+        r.U[k] = from_next_lane(r.P[k]);
+        r.Pp[k] = shr1(r.P[k]);
+        r.Pm[k] = shl1(r.P[k]);
+    }
+}
+
+template <int K, bool TOP>
+struct Walk3d {
+    uint32_t wx0, wx2, wyp[3], wym[3], Wm[3][3];   // wins of (z, y) known so far
+    uint32_t ex_x[3], ey[3];                       // neighbour existence along x and y
+
+    // xex: existence of the window's voxels; ym/yp: rows y-1 / y+1 exist.
+    __device__ __forceinline__ void begin(uint32_t xex, bool ym, bool yp)
+    {
+        ex_x[0] = xex << 1;
+        ex_x[1] = 0xffffffffu;
+        ex_x[2] = xex >> 1;
+        ey[0] = ym ? 0xffffffffu : 0u;
+        ey[1] = 0xffffffffu;
+        ey[2] = yp ? 0xffffffffu : 0u;
+        wx0 = wx2 = 0;
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            wyp[d] = wym[d] = 0;
+            Wm[0][d] = Wm[1][d] = Wm[2][d] = 0;
+        }
+    }
+
+    // From plane z (rows a) to plane z+1 (rows b).  EDGE: apply the existence
+    // masks (zp: plane z+1 exists, z_ok: plane z exists); without EDGE every
+    // neighbour exists (interior tile).  When `emit_z` (warp-uniform), calls
+    // emit(mask, S, N, a.P) for plane z: output voxels with a nonzero count,
+    // count = 1 + S - N before the top-cell sign.  Warp-collective.
+    template <bool EDGE, class Emit>
+    __device__ __forceinline__ void step(const Rows3<K> &a, const Rows3<K> &b, bool zp, bool z_ok, bool emit_z,
+                                         uint32_t out_x, Emit &&emit)
+    {
+        // plane z against plane z+1 (z earlier): H0[d][x] = A[x-d] vs B[x],
+        // Hp[d][x] = A[x-d] vs Bu[x], K2[d][x] = Au[x] vs B[x+d]
+        uint32_t H0[3], Hp[3], K2[3];
+        H0[0] = beats_later<K, TOP>(a.Pp, b.P);
+        H0[1] = beats_later<K, TOP>(a.P, b.P);
+        H0[2] = beats_later<K, TOP>(a.Pm, b.P);
+        Hp[0] = beats_later<K, TOP>(a.Pp, b.U);
+        Hp[1] = beats_later<K, TOP>(a.P, b.U);
+        Hp[2] = beats_later<K, TOP>(a.Pm, b.U);
+        K2[0] = beats_later<K, TOP>(a.U, b.Pm);
+        K2[1] = beats_later<K, TOP>(a.U, b.P);
+        K2[2] = beats_later<K, TOP>(a.U, b.Pp);
+        // in-plane pairs of plane z+1: E[x] = B[x-1] vs B[x], F[d][x] = B[x-d] vs Bu[x]
+        const uint32_t E = beats_later<K, TOP>(b.Pm, b.P);
+        uint32_t F[3];
+        F[0] = beats_later<K, TOP>(b.Pp, b.U);
+        F[1] = beats_later<K, TOP>(b.P, b.U);
+        F[2] = beats_later<K, TOP>(b.Pm, b.U);
+        uint32_t Hp_dn[3], K2_dn[3], F_dn[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            Hp_dn[d] = from_prev_lane(Hp[d]);
+            K2_dn[d] = from_prev_lane(K2[d]);
+            F_dn[d] = from_prev_lane(F[d]);
+        }
+        const uint32_t ez_p = (!EDGE || zp) ? 0xffffffffu : 0u;
+        const uint32_t ez_m1 = (!EDGE || z_ok) ? 0xffffffffu : 0u;
+        auto ex = [&](int i) { return EDGE ? ex_x[i] : 0xffffffffu; };
+        auto eyy = [&](int i) { return EDGE ? ey[i] : 0xffffffffu; };
+        if (emit_z) {
+            uint32_t w[3][3][3];
+            w[2][1][0] = at_offset<-1>(H0[0]);
+            w[2][1][1] = H0[1];
+            w[2][1][2] = at_offset<+1>(H0[2]);
+            w[2][2][0] = at_offset<-1>(Hp[0]);
+            w[2][2][1] = Hp[1];
+            w[2][2][2] = at_offset<+1>(Hp[2]);
+            w[2][0][0] = K2_dn[0];   // row y-1 of z+1 at x-1: lane y-1's Au (= our A) vs its B[x-1]
+            w[2][0][1] = K2_dn[1];
+            w[2][0][2] = K2_dn[2];
+#pragma unroll
+            for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+                for (int dx = 0; dx < 3; ++dx) {
+                    if (EDGE) w[2][dy][dx] = with_exist<TOP>(w[2][dy][dx], ez_p & ey[dy] & ex_x[dx]);
+                    w[0][dy][dx] = Wm[dy][dx];
+                }
+            w[1][1][0] = wx0;
+            w[1][1][1] = 0;
+            w[1][1][2] = wx2;
+#pragma unroll
+            for (int dx = 0; dx < 3; ++dx) {
+                w[1][0][dx] = wym[dx];
+                w[1][2][dx] = wyp[dx];
+            }
+            uint32_t S[4], N[4];
+            const uint32_t m = bs::kappa3d(w, S, N) & out_x;
+            emit(m, S, N, a.P);
+        }
+        // wins of (z+1, y) over plane z (an earlier neighbour wins ties)
+        Wm[1][0] = with_exist<TOP>(~H0[2], ez_m1 & eyy(1) & ex(0));
+        Wm[1][1] = with_exist<TOP>(~H0[1], ez_m1 & eyy(1));
+        Wm[1][2] = with_exist<TOP>(~H0[0], ez_m1 & eyy(1) & ex(2));
+        Wm[2][0] = with_exist<TOP>(~at_offset<-1>(K2[2]), ez_m1 & eyy(2) & ex(0));
+        Wm[2][1] = with_exist<TOP>(~K2[1], ez_m1 & eyy(2));
+        Wm[2][2] = with_exist<TOP>(~at_offset<+1>(K2[0]), ez_m1 & eyy(2) & ex(2));
+        Wm[0][0] = with_exist<TOP>(~Hp_dn[2], ez_m1 & eyy(0) & ex(0));
+        Wm[0][1] = with_exist<TOP>(~Hp_dn[1], ez_m1 & eyy(0));
+        Wm[0][2] = with_exist<TOP>(~Hp_dn[0], ez_m1 & eyy(0) & ex(2));
+        // in-plane wins of (z+1, y)
+        wx2 = with_exist<TOP>(at_offset<+1>(E), ex(2));
+        wx0 = with_exist<TOP>(~E, ex(0));
+        wyp[0] = with_exist<TOP>(at_offset<-1>(F[0]), eyy(2) & ex(0));
+        wyp[1] = with_exist<TOP>(F[1], eyy(2));
+        wyp[2] = with_exist<TOP>(at_offset<+1>(F[2]), eyy(2) & ex(2));
+        wym[0] = with_exist<TOP>(~F_dn[2], eyy(0) & ex(0));
+        wym[1] = with_exist<TOP>(~F_dn[1], eyy(0));
+        wym[2] = with_exist<TOP>(~F_dn[0], eyy(0) & ex(2));
+    }
+};
+
+// ------------------------------------------------------------------ 2D
+
+template <int K, bool TOP>
+struct Walk2d {
+    uint32_t A[K];                 // planes of row y
+    uint32_t wx0, wx2, wym[3];     // wins of row y known so far
+    uint32_t ex_x[3];
+
+    __device__ __forceinline__ void begin(const uint32_t *P, uint32_t xex)
+    {
+        ex_x[0] = xex << 1;
+        ex_x[1] = 0xffffffffu;
+        ex_x[2] = xex >> 1;
+#pragma unroll
+        for (int k = 0; k < K; ++k) A[k] = P[k];
+        wx0 = wx2 = 0;
+        wym[0] = wym[1] = wym[2] = 0;
+    }
+
+    // Advance to row y+1 (window B).  yp: row y+1 exists; y_ok: row y exists.
+    // When emit_y, calls emit(mask, Q, F, A) for row y with count = 1 + Q - F.
+    template <class Emit>
+    __device__ __forceinline__ void step(const uint32_t *B, bool yp, bool y_ok, bool emit_y, uint32_t out_x,
+                                         Emit &&emit)
+    {
+        uint32_t H[3], E;
+        {
+            uint32_t Ap[K], Am[K], Bp[K], Bm[K];
+            shifted<K>(A, Ap, Am);
+            shifted<K>(B, Bp, Bm);
+            H[0] = beats_later<K, TOP>(Ap, B);  // [x]: A[x+1] vs B[x]
+            H[1] = beats_later<K, TOP>(A, B);
+            H[2] = beats_later<K, TOP>(Am, B);  // [x]: A[x-1] vs B[x]
+            E = beats_later<K, TOP>(Bm, B);     // [x]: B[x-1] vs B[x]
+        }
+        const uint32_t ey_p = yp ? 0xffffffffu : 0u;
+        const uint32_t ey_m1 = y_ok ? 0xffffffffu : 0u;
+        if (emit_y) {
+            uint32_t w[3][3];
+            w[0][0] = wym[0];
+            w[0][1] = wym[1];
+            w[0][2] = wym[2];
+            w[1][0] = wx0;
+            w[1][1] = 0;
+            w[1][2] = wx2;
+            w[2][0] = with_exist<TOP>(at_offset<-1>(H[0]), ey_p & ex_x[0]);
+            w[2][1] = with_exist<TOP>(H[1], ey_p);
+            w[2][2] = with_exist<TOP>(at_offset<+1>(H[2]), ey_p & ex_x[2]);
+            uint32_t F[3], Q[3];
+            const uint32_t m = bs::kappa2d(w, F, Q) & out_x;
+            emit(m, Q, F, A);
+        }
+#pragma unroll
+        for (int dx = 0; dx < 3; ++dx) wym[dx] = with_exist<TOP>(~H[2 - dx], ey_m1 & ex_x[dx]);
+        wx2 = with_exist<TOP>(at_offset<+1>(E), ex_x[2]);
+        wx0 = with_exist<TOP>(~E, ex_x[0]);
+#pragma unroll
+        for (int k = 0; k < K; ++k) A[k] = B[k];
+    }
+};
+
+}  // namespace walk
+}  // namespace ecc
