@@ -197,6 +197,117 @@ def run_reference(args):
     return 0
 
 
+def run_batched(args):
+    """Uneven batch (4096 2D + 256 3D uint8 smoothed fields): one graph launch
+    of the persistent batch kernel vs one stencil launch per image."""
+    import numpy as np
+    import torch
+
+    import paper_2203_09087_gb300 as ecc
+    import synth
+    specs = synth.batch_specs()
+    imgs = synth.batch_images(specs, device="cuda")
+    total = sum(int(i.numel()) for i in imgs)
+    out = torch.empty((len(imgs), 256), dtype=torch.int64, device="cuda")
+    res = {"workload": "4096 2D (H,W ~ U{64..1024}) + 256 3D (sides ~ U{32..256}) uint8, sigma ~ U[1,6], seed 3",
+           "voxels": total}
+    ref = None
+    for name, flags in (("batched", 0), ("per_image", ecc.ECC_FLAG_BATCH_PER_IMAGE)):
+        plan = ecc.ecc_plan("u8", 0, 255, max_images=len(imgs), max_voxels=total, flags=flags)
+        for _ in range(3):
+            ecc.ecc_compute_batch(plan, imgs, out)
+        ecc.ecc_status_get(plan)
+        got = out.cpu().numpy()
+        if ref is None:
+            ref = got
+        assert np.array_equal(ref, got)
+        reps = 5
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        s.record()
+        for _ in range(reps):
+            ecc.ecc_compute_batch(plan, imgs, out)
+        e.record()
+        torch.cuda.synchronize()
+        ms = s.elapsed_time(e) / reps
+        res[name] = {"ms": ms, "gvox_s": total / ms / 1e6, "launches": ecc.ecc_plan_last_launches(plan)}
+    res["speedup"] = res["per_image"]["ms"] / res["batched"]["ms"]
+    return res
+
+
+def run_serving(args):
+    """Poisson stream of mixed 2D/3D uint8/uint16 requests (crops of resident
+    seeded fields): p50/p99 latency at the nominal rate, and throughput of a
+    saturating replay of the same list against the sequential plain path."""
+    import threading
+
+    import numpy as np
+    import torch
+
+    import paper_2203_09087_gb300 as ecc
+    import synth
+    reqs = synth.poisson_requests(2000.0, args.serve_seconds)
+    base2d = synth.smoothed_field((4096, 4096), 3.0, np.uint8, seed=41, device="cuda")
+    base8 = synth.smoothed_field((768, 768, 768), 3.0, np.uint8, seed=42, device="cuda")
+    base16 = synth.smoothed_field((768, 768, 768), 3.0, np.uint16, seed=43, device="cuda")
+    rng = np.random.default_rng(4)
+    views = []
+    for r in reqs:
+        s = r["shape"][0]
+        if len(r["shape"]) == 2:
+            o = [int(rng.integers(0, 4096 - s + 1)) for _ in range(2)]
+            o[1] -= o[1] % 16
+            views.append((base2d[o[0]:o[0] + s, o[1]:o[1] + s], 255))
+        else:
+            base, hi = (base8, 255) if r["dtype"] == "u8" else (base16, 65535)
+            o = [int(rng.integers(0, 768 - s + 1)) for _ in range(3)]
+            o[2] -= o[2] % 16
+            views.append((base[o[0]:o[0] + s, o[1]:o[1] + s, o[2]:o[2] + s], hi))
+    vox = sum(int(v.numel()) for v, _ in views)
+
+    def serve(replay_rate: bool):
+        srv = ecc.ecc_server_create(120 << 30, n_streams=4, max_batch=64)
+        outs = [np.zeros(hi + 1, np.int64) for _, hi in views]
+        tickets = [0] * len(views)
+        t0 = time.perf_counter()
+        for i, ((v, hi), r) in enumerate(zip(views, reqs)):
+            if replay_rate:
+                delay = r["t"] - (time.perf_counter() - t0)
+                if delay > 0:
+                    time.sleep(delay)
+            tickets[i] = ecc.ecc_submit(srv, v, 0, hi, out=outs[i])
+        for t in tickets:
+            assert ecc.ecc_wait(srv, t, 600_000_000) == ecc.ECC_OK
+        wall = time.perf_counter() - t0
+        st = ecc.ecc_server_stats(srv)
+        ecc.ecc_server_destroy(srv)
+        return wall, st, outs
+
+    wall_rt, st_rt, outs_rt = serve(True)
+    wall_sat, st_sat, outs_sat = serve(False)
+    # sequential plain path: one ecc_compute per request, synchronized
+    plans = {255: ecc.ecc_plan("u8", 0, 255, max_voxels=1 << 31), 65535: ecc.ecc_plan("u16", 0, 65535, max_voxels=1 << 31)}
+    outs_seq = []
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for v, hi in views:
+        o = ecc.ecc_compute(plans[hi], v)
+        outs_seq.append(o.cpu().numpy())
+    wall_seq = time.perf_counter() - t0
+    same = all(np.array_equal(a, b) and np.array_equal(a, c) for a, b, c in zip(outs_seq, outs_rt, outs_sat))
+    return {"workload": f"Poisson 2000 req/s x {args.serve_seconds:g} s (seed 4), 70% 2D u8 128^2-4096^2, "
+                        "30% 3D u8/u16 64^3-768^3, crops of resident seeded fields",
+            "requests": len(views), "voxels": vox,
+            "nominal": {"p50_ms": st_rt["p50_us"] / 1e3, "p99_ms": st_rt["p99_us"] / 1e3,
+                        "max_ms": st_rt["max_us"] / 1e3, "launches": st_rt["launches"],
+                        "gvox_s": vox / wall_rt / 1e9},
+            "saturating": {"gvox_s": vox / wall_sat / 1e9, "p50_ms": st_sat["p50_us"] / 1e3,
+                           "p99_ms": st_sat["p99_us"] / 1e3, "launches": st_sat["launches"]},
+            "sequential_plain": {"gvox_s": vox / wall_seq / 1e9},
+            "served_vs_sequential": wall_seq / wall_sat,
+            "identical_results": bool(same)}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -207,6 +318,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
     ap.add_argument("--extras", action="store_true", help="also run the batched and serving workloads")
     ap.add_argument("--shape", default="512,512,512")
+    ap.add_argument("--serve-seconds", type=float, default=8.0,
+                    help="duration of the Poisson request stream in --extras (configuration: 60)")
     ap.add_argument("--quick", action="store_true",
                     help="profiler runs: no one-second warm-up floor, no e2e and CPU legs")
     args = ap.parse_args()
@@ -308,9 +421,8 @@ def main():
     if rank == 0 and not args.no_cpu and not args.quick:
         line["cpu_baseline"] = cpu_oracle_sample(vol.cpu().numpy())
     if args.extras and rank == 0:
-        from bench_extras import run_batched, run_serving  # noqa
-        line["batched"] = run_batched()
-        line["serving"] = run_serving()
+        line["batched"] = run_batched(args)
+        line["serving"] = run_serving(args)
     if rank == 0:
         print(json.dumps(line))
     if dist:

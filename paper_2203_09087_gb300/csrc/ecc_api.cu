@@ -109,7 +109,8 @@ static cudaError_t launch_stencil_untimed(ecc_plan_s *p, const Geom &g, int64_t 
     const bool want_bitslice = !(p->d.flags & ECC_FLAG_KERNEL_DIRECT);
     if (want_bitslice && bitslice_supported(g)) {
         const int tp = p->tune_param(g);
-        cudaError_t e = launch_bitslice(g, ob, oe, h, p->d.complex_mode, range, p->status, p->num_sms, tp, s);
+        cudaError_t e =
+            launch_bitslice(g, ob, oe, h, p->d.complex_mode, range, p->status, p->sched, p->num_sms, tp, s);
         if (e != cudaErrorNotSupported) {
             ++p->last_launches;
             return e;

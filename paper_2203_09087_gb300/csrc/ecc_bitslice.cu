@@ -65,6 +65,7 @@ struct Cfg {
 };
 
 struct Bs3dArgs {
+    unsigned int *sched;     // [0] next item, [1] finished CTAs (reset by the last CTA)
     int64_t nx, ny, nz;
     int64_t z_begin, z_end;  // outer range of output planes
     int32_t ntx, nty, nzc;   // tiles along x, y and z-chunks
@@ -173,10 +174,21 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
 // NW compute warps and one producer warp.  Stage s of the ring has a "full"
 // barrier (the TMA's transaction count) and an "empty" barrier (one arrival
 // per compute warp once it has copied its window out of the stage), so the
-// warps never wait for each other, only for data.
+// warps never wait for each other, only for data.  The producer claims items
+// from a global counter (dynamic load balance) and tags every stage with its
+// item; a stage tagged -1 (no copy, plain arrival) ends the CTA.  The last
+// CTA to finish resets the counter for the next launch.
+// Blocks per SM the register allocation must allow: the walk is latency
+// bound, so more resident warps beat more registers per thread.
+template <typename T, int NW>
+constexpr int bs3d_min_blocks()
+{
+    return sizeof(T) == 1 ? (NW == 3 ? 5 : (NW == 4 ? 4 : 2)) : (NW == 3 ? 3 : (NW == 4 ? 2 : 1));
+}
+
 template <typename T, int NW, bool TOP, int HREP>
-__global__ void __launch_bounds__((NW + 1) * 32) bs3d_kernel(const __grid_constant__ CUtensorMap tmap,
-                                                             const Bs3dArgs a)
+__global__ void __launch_bounds__((NW + 1) * 32, bs3d_min_blocks<T, NW>())
+    bs3d_kernel(const __grid_constant__ CUtensorMap tmap, const Bs3dArgs a)
 {
     using C = Cfg<T>;
     constexpr int K = C::K, S = C::S, ES = C::ES;
@@ -191,8 +203,10 @@ __global__ void __launch_bounds__((NW + 1) * 32) bs3d_kernel(const __grid_consta
     uint64_t *empty = full + S;
     int *hist = reinterpret_cast<int *>(empty + S);
     __shared__ int s_abort;
+    __shared__ int s_item[S];        // item of the plane held by each stage, -1 = end
     __shared__ long long s_consumed[NW];
     __shared__ long long s_issued;
+    __shared__ int s_last;
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (a.smem_hist)
@@ -225,25 +239,38 @@ __global__ void __launch_bounds__((NW + 1) * 32) bs3d_kernel(const __grid_consta
         // ------------------------------------------------------ producer warp
         if (lane == 0) {
             int64_t g = 0;
-            for (int item = blockIdx.x; item < a.nitems; item += gridDim.x) {
-                int xt, yt;
-                int64_t zb, ze;
-                decode(item, xt, yt, zb, ze);
+            bool live = true;
+            while (live) {
+                const int item = (int)atomicAdd(a.sched, 1u);
+                const bool more = item < a.nitems;
+                int xt = 0, yt = 0;
+                int64_t zb = 0, ze = -1;
+                if (more) decode(item, xt, yt, zb, ze);
                 const int bx = (int)box_x(xt);
                 const int y0 = yt * kOut - 1;
-                for (int64_t z = zb - 1; z <= ze; ++z, ++g) {
+                // planes zb-1 .. ze, or one terminal stage
+                for (int64_t z = zb - 1; more ? z <= ze : z == zb - 1; ++z, ++g) {
                     const int s = (int)(g % S);
                     if (g >= S && !mbar_wait(&empty[s], (uint32_t)(((g / S) - 1) & 1))) {
                         atomicOr(a.status, DEV_TIMEOUT);
                         atomicExch(&s_abort, 1);
+                        live = false;
                         break;
                     }
-                    if (*(volatile int *)&s_abort) break;
-                    mbar_expect_tx(&full[s], STAGE);
-                    tma_load_3d(stages + (size_t)s * STAGE, &tmap, bx, y0, (int)z, &full[s]);
+                    if (*(volatile int *)&s_abort) {
+                        live = false;
+                        break;
+                    }
+                    s_item[s] = more ? item : -1;
+                    if (more) {
+                        mbar_expect_tx(&full[s], STAGE);
+                        tma_load_3d(stages + (size_t)s * STAGE, &tmap, bx, y0, (int)z, &full[s]);
+                    } else {
+                        mbar_arrive(&full[s]);
+                        live = false;
+                    }
                     s_issued = g + 1;
                 }
-                if (*(volatile int *)&s_abort) break;
             }
         }
     } else {
@@ -251,34 +278,47 @@ __global__ void __launch_bounds__((NW + 1) * 32) bs3d_kernel(const __grid_consta
         int *my_hist = hist + (warp % HREP) * a.h.nbins;
         int64_t g = 0;
         bool ok = true;
-        auto fetch = [&](walk::Rows3<K> &r) {
-            // wait for step g's stage, copy this lane's window, release the stage
+        auto wait_full = [&]() -> int {
             const int s = (int)(g % S);
-            if (ok && !mbar_wait(&full[s], (uint32_t)((g / S) & 1))) {
+            if (!mbar_wait(&full[s], (uint32_t)((g / S) & 1))) {
                 if (lane == 0) {
                     atomicOr(a.status, DEV_TIMEOUT);
                     atomicExch(&s_abort, 1);
                 }
                 ok = false;
+                return -1;
             }
-            if (ok) {
-                load_window<T>(stages + (size_t)s * STAGE + lane * BWB, r.off, r.P);
+            return s;
+        };
+        int off = 0;
+        auto fetch = [&](walk::Rows3<K> &r) {
+            // copy this lane's window of step g's stage, release the stage
+            const int s = ok ? wait_full() : -1;
+            if (s >= 0) {
+                load_window<T>(stages + (size_t)s * STAGE + lane * BWB, off, r.P);
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&empty[s]);
             }
             ++g;
             walk::complete_rows<K>(r);
         };
-        for (int item = blockIdx.x; item < a.nitems && ok; item += gridDim.x) {
+        while (ok) {
+            // the stage of the next item's first plane says which item it is
+            const int s0 = wait_full();
+            if (s0 < 0) break;
+            const int item = s_item[s0];
+            if (item < 0) {
+                ++g;
+                break;
+            }
             int xt, yt;
             int64_t zb, ze;
             decode(item, xt, yt, zb, ze);
             const int64_t X0 = (int64_t)xt * (kOut * NW);
-            const int64_t bx = box_x(xt);
             const int64_t y0 = (int64_t)yt * kOut - 1;
             const int64_t y = y0 + lane;
             const int64_t xw = X0 + kOut * warp - 1;  // voxel of window bit 0
-            const int off = (int)((xw - bx) * ES);
+            off = (int)((xw - box_x(xt)) * ES);
             const uint32_t xex = walk::x_exist_mask(xw, a.nx);
             const bool lane_out = lane >= 1 && lane <= kOut && y < a.ny;
             const uint32_t out_x = lane_out ? (xex & 0x7ffffffeu) : 0u;
@@ -305,8 +345,7 @@ __global__ void __launch_bounds__((NW + 1) * 32) bs3d_kernel(const __grid_consta
                 }
             };
             walk::Rows3<K> r0, r1;
-            r0.off = r1.off = off;
-            fetch(r0);  // plane zb-1
+            fetch(r0);  // plane zb-1 (its full barrier already passed)
             int64_t z1 = zb;
             auto advance = [&](const walk::Rows3<K> &cur, const walk::Rows3<K> &nxt) {
                 const bool zp = z1 < a.nz, zok = z1 - 1 >= 0;
@@ -344,6 +383,16 @@ __global__ void __launch_bounds__((NW + 1) * 32) bs3d_kernel(const __grid_consta
             for (int r = 0; r < HREP; ++r) v += hist[r * a.h.nbins + i];
             if (v) atomicAdd(a.h.acc + i, (unsigned long long)(long long)v);
         }
+    // the last CTA resets the item counter for the next launch
+    if (tid == 0) {
+        __threadfence();
+        s_last = atomicAdd(a.sched + 1, 1u) == gridDim.x - 1;
+        if (s_last) {
+            a.sched[0] = 0u;
+            a.sched[1] = 0u;
+            __threadfence();
+        }
+    }
 }
 
 // ----------------------------------------------------------------- 2D kernel
@@ -512,7 +561,7 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
 
 template <typename T, int NW, bool TOP, int HREP>
 cudaError_t launch_t(const Geom &g, int64_t zb, int64_t ze, const HistDst &h, bool range_check,
-                     unsigned int *status, int num_sms, cudaStream_t s)
+                     unsigned int *status, unsigned int *sched, int num_sms, cudaStream_t s)
 {
     using C = Cfg<T>;
     constexpr int BWB = box_bytes(NW, C::ES);
@@ -530,6 +579,7 @@ cudaError_t launch_t(const Geom &g, int64_t zb, int64_t ze, const HistDst &h, bo
     if (r != CUDA_SUCCESS) return cudaErrorNotSupported;
 
     Bs3dArgs a{};
+    a.sched = sched;
     a.nx = g.nx;
     a.ny = g.ny;
     a.nz = g.nz;
@@ -555,6 +605,12 @@ cudaError_t launch_t(const Geom &g, int64_t zb, int64_t ze, const HistDst &h, bo
         }
         attr_smem = smem;
     }
+    static bool carveout = false;
+    if (!carveout) {  // let the ring stages of several CTAs share an SM
+        cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        cudaGetLastError();
+        carveout = true;
+    }
     if (occ_smem != smem || per_sm == 0) {
         cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, (NW + 1) * 32, smem);
         if (e != cudaSuccess) return e;
@@ -564,8 +620,8 @@ cudaError_t launch_t(const Geom &g, int64_t zb, int64_t ze, const HistDst &h, bo
     const int64_t ctas_max = (int64_t)num_sms * per_sm;
     const int64_t cols = (int64_t)a.ntx * a.nty;
     const int64_t depth = ze - zb;
-    // z-chunks: enough items for about three per CTA, each chunk >= 8 planes
-    int64_t nzc = (3 * ctas_max + cols - 1) / cols;
+    // z-chunks: several items per CTA (they are handed out dynamically), each >= 8 planes
+    int64_t nzc = (6 * ctas_max + cols - 1) / cols;
     if (nzc > (depth + 7) / 8) nzc = (depth + 7) / 8;
     if (nzc < 1) nzc = 1;
     a.zchunk = (int32_t)((depth + nzc - 1) / nzc);
@@ -580,14 +636,14 @@ cudaError_t launch_t(const Geom &g, int64_t zb, int64_t ze, const HistDst &h, bo
 
 template <int NW, int HREP>
 cudaError_t launch_nw(const Geom &g, int64_t zb, int64_t ze, const HistDst &h, int mode, bool rc, unsigned int *st,
-                      int sms, cudaStream_t s)
+                      unsigned int *sched, int sms, cudaStream_t s)
 {
     const bool top = mode == ECC_TOPCELL_MIN;
     if (g.esize == 1)
-        return top ? launch_t<unsigned char, NW, true, HREP>(g, zb, ze, h, rc, st, sms, s)
-                   : launch_t<unsigned char, NW, false, HREP>(g, zb, ze, h, rc, st, sms, s);
-    return top ? launch_t<unsigned short, NW, true, HREP>(g, zb, ze, h, rc, st, sms, s)
-               : launch_t<unsigned short, NW, false, HREP>(g, zb, ze, h, rc, st, sms, s);
+        return top ? launch_t<unsigned char, NW, true, HREP>(g, zb, ze, h, rc, st, sched, sms, s)
+                   : launch_t<unsigned char, NW, false, HREP>(g, zb, ze, h, rc, st, sched, sms, s);
+    return top ? launch_t<unsigned short, NW, true, HREP>(g, zb, ze, h, rc, st, sched, sms, s)
+               : launch_t<unsigned short, NW, false, HREP>(g, zb, ze, h, rc, st, sched, sms, s);
 }
 
 }  // namespace
@@ -603,9 +659,11 @@ bool bitslice_supported(const Geom &g)
     return encode_fn() != nullptr;
 }
 
-// tune_param: 0 = choose by x-waste; otherwise the windows per CTA (3, 4 or 6).
+// tune_param: 0 = choose by wasted columns; otherwise 10 * (windows per CTA)
+// + (shared histogram copies): 61, 62, 42, 31 (the autotuner's candidates).
 cudaError_t launch_bitslice(const Geom &g, int64_t outer_begin, int64_t outer_end, const HistDst &h, int mode,
-                            bool range_check, unsigned int *status, int num_sms, int tune_param, cudaStream_t s)
+                            bool range_check, unsigned int *status, unsigned int *sched, int num_sms, int tune_param,
+                            cudaStream_t s)
 {
     if (outer_end <= outer_begin) return cudaSuccess;
     if (!bitslice_supported(g)) return cudaErrorNotSupported;
@@ -617,22 +675,25 @@ cudaError_t launch_bitslice(const Geom &g, int64_t outer_begin, int64_t outer_en
         return top ? launch_2d_t<unsigned short, true>(g, outer_begin, outer_end, h, range_check, status, num_sms, s)
                    : launch_2d_t<unsigned short, false>(g, outer_begin, outer_end, h, range_check, status, num_sms, s);
     }
-    int nw = tune_param;
-    if (nw != 3 && nw != 4 && nw != 6) {
+    int tp = tune_param;
+    if (tp != 61 && tp != 62 && tp != 42 && tp != 31) {
         // fewest wasted columns; ties to the wider tile
         int64_t best = -1;
-        for (int cand : {6, 4, 3}) {
-            const int64_t w = kOut * cand;
+        for (int cand : {62, 42, 31}) {
+            const int64_t w = kOut * (cand / 10);
             const int64_t waste = (g.nx + w - 1) / w * w - g.nx;
             if (best < 0 || waste < best) {
                 best = waste;
-                nw = cand;
+                tp = cand;
             }
         }
     }
-    if (nw == 6) return launch_nw<6, 2>(g, outer_begin, outer_end, h, mode, range_check, status, num_sms, s);
-    if (nw == 4) return launch_nw<4, 2>(g, outer_begin, outer_end, h, mode, range_check, status, num_sms, s);
-    return launch_nw<3, 1>(g, outer_begin, outer_end, h, mode, range_check, status, num_sms, s);
+    switch (tp) {
+    case 61: return launch_nw<6, 1>(g, outer_begin, outer_end, h, mode, range_check, status, sched, num_sms, s);
+    case 62: return launch_nw<6, 2>(g, outer_begin, outer_end, h, mode, range_check, status, sched, num_sms, s);
+    case 42: return launch_nw<4, 2>(g, outer_begin, outer_end, h, mode, range_check, status, sched, num_sms, s);
+    default: return launch_nw<3, 1>(g, outer_begin, outer_end, h, mode, range_check, status, sched, num_sms, s);
+    }
 }
 
 }  // namespace ecc

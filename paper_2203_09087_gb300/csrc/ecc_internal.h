@@ -84,9 +84,11 @@ cudaError_t launch_direct(const Geom &g, int64_t outer_begin, int64_t outer_end,
 // Bit-sliced stencil + histogram (3D and 2D, uint8 / uint16, both complexes).
 // Returns cudaErrorNotSupported when the geometry does not qualify.
 bool bitslice_supported(const Geom &g);
+// sched: two device words, zero before the first launch; the kernel leaves
+// them zero again (its dynamic item counter and finished-CTA count).
 cudaError_t launch_bitslice(const Geom &g, int64_t outer_begin, int64_t outer_end, const HistDst &h,
-                            int complex_mode, bool range_check, unsigned int *status, int num_sms,
-                            int tune_param, cudaStream_t s);
+                            int complex_mode, bool range_check, unsigned int *status, unsigned int *sched,
+                            int num_sms, int tune_param, cudaStream_t s);
 
 // Segmented inclusive scan of n_seg * nbins int64 values (segment i =
 // elements [i*nbins, (i+1)*nbins)).  Reads acc, writes ecc (and vcec if not

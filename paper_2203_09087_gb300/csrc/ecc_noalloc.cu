@@ -35,7 +35,8 @@ constexpr int kNoallocMaxBins = 65536;
 constexpr int kNoallocTiles = (kNoallocMaxBins + kScanTile - 1) / kScanTile;
 
 // Layout (8-byte words): [0, kNoallocMaxBins) accumulator;
-// then 32 words for the status word and the two scan counters;
+// then 32 words for the status word (32-bit word 0), the two scan counters
+// (words 2, 3) and the stencil's work counters (words 4, 5);
 // then kNoallocTiles words of tile status (ints, 2 per word) rounded up;
 // then 2 * kNoallocTiles words of tile values.
 constexpr int kAccWords = kNoallocMaxBins;
@@ -127,7 +128,7 @@ extern "C" ecc_status ecc_compute_noalloc(const ecc_image *img, int32_t lo, int3
     const int64_t outer = g.ndim == 3 ? g.nz : g.ny;
     e = cudaErrorNotSupported;
     if (!(flags & ECC_FLAG_KERNEL_DIRECT) && bitslice_supported(g))
-        e = launch_bitslice(g, 0, outer, h, complex_mode, range, status, sms, 0, s);
+        e = launch_bitslice(g, 0, outer, h, complex_mode, range, status, ctl + 4, sms, 0, s);
     if (e == cudaErrorNotSupported) e = launch_direct(g, 0, outer, h, complex_mode, range, status, sms, s);
     if (e != cudaSuccess) return cuda_fail(e, "ecc_compute_noalloc: stencil launch");
     e = launch_scan(acc, reinterpret_cast<long long *>(d_ecc), reinterpret_cast<long long *>(d_vcec), 1,

@@ -34,6 +34,7 @@ ecc_status ecc_plan_s::allocate()
     status = reinterpret_cast<unsigned int *>(b);
     b += status_bytes;
     scan_counters = reinterpret_cast<unsigned int *>(b);
+    sched = scan_counters + 16;  // same 256-byte block, separate words
     b += counters_bytes;
     tile_status = reinterpret_cast<int *>(b);
     b += tstat_bytes;

@@ -29,6 +29,7 @@ struct ecc_plan_s {
     unsigned long long *acc = nullptr;   // [max_images * nbins] int64, kept zero between calls
     unsigned int *status = nullptr;      // device status word (ecc::DEV_*)
     unsigned int *scan_counters = nullptr;
+    unsigned int *sched = nullptr;       // stencil work counter (2 words, self-resetting)
     int *tile_status = nullptr;
     long long *tile_value = nullptr;
     int32_t max_tiles = 0;

@@ -1,4 +1,252 @@
-// ecc_tune.cu -- tile-parameter selection (autotuner).
+// ecc_tune.cu -- the autotuner: picks tile shapes and histogram
+// privatization depth by timing candidates on the device.
+//
+// Keys: GPU name, SM count, element type and complex.  For each key it
+// chooses
+//   * the 3D bit-sliced kernel's windows per CTA and number of shared
+//     histogram copies (candidates 6x1, 6x2, 4x2, 3x1), timed on a synthetic
+//     352x150x128 volume;
+//   * the batched kernel's rows per 2D tile (16, 32, 64) and planes per 3D
+//     tile (8, 16, 32), timed on a synthetic uneven batch.
+// Results are kept for the process and appended to a text cache
+// ($ECC_TUNE_CACHE, else $HOME/.cache/ecc_gb300/tune.txt), so a GPU model is
+// tuned once.  ECC_FLAG_NO_AUTOTUNE (or ECC_TUNE=off) keeps the defaults.
+#include <cuda_runtime.h>
+
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <fstream>
+#include <map>
+#include <mutex>
+#include <sstream>
+#include <string>
+#include <sys/stat.h>
+#include <vector>
+
 #include "ecc_plan.h"
 
-void ecc_plan_s::autotune() {}
+namespace ecc {
+namespace {
+
+// "<key>|3d" -> {tp3d, 0}; "<key>|batch" -> {chunk2d, chunk3d}
+struct Choice {
+    int a = 0, b = 0;
+};
+
+std::mutex g_tune_mu;
+std::map<std::string, Choice> g_tuned;
+bool g_loaded = false;
+
+std::string cache_path()
+{
+    if (const char *p = std::getenv("ECC_TUNE_CACHE")) return p;
+    const char *home = std::getenv("HOME");
+    return std::string(home ? home : "/tmp") + "/.cache/ecc_gb300/tune.txt";
+}
+
+void load_cache()
+{
+    if (g_loaded) return;
+    g_loaded = true;
+    std::ifstream f(cache_path());
+    std::string line;
+    while (std::getline(f, line)) {
+        std::istringstream is(line);
+        std::string key;
+        Choice c;
+        if (is >> key >> c.a >> c.b) g_tuned[key] = c;
+    }
+}
+
+void save_choice(const std::string &key, const Choice &c)
+{
+    const std::string path = cache_path();
+    std::string dir = path.substr(0, path.rfind('/'));
+    for (size_t i = 1; i <= dir.size(); ++i)
+        if (i == dir.size() || dir[i] == '/') mkdir(dir.substr(0, i).c_str(), 0755);
+    std::ofstream f(path, std::ios::app);
+    if (f) f << key << ' ' << c.a << ' ' << c.b << '\n';
+}
+
+// Smooth-ish synthetic field: a ramp plus blocky hash noise, every value in [lo, hi].
+__global__ void synth_fill(unsigned char *d, int64_t n, int esize, int nx, int ny, int lo, int hi)
+{
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int x = (int)(i % nx), y = (int)((i / nx) % ny), z = (int)(i / ((int64_t)nx * ny));
+        unsigned h = (unsigned)((x >> 3) * 73856093u) ^ (unsigned)((y >> 3) * 19349663u) ^ (unsigned)((z >> 3) * 83492791u);
+        h ^= h >> 13;
+        h *= 0x5bd1e995u;
+        const unsigned span = (unsigned)(hi - lo + 1);
+        const unsigned v = lo + ((unsigned)(x + y + z) + (h & 63u)) % span;
+        if (esize == 1)
+            d[i] = (unsigned char)v;
+        else
+            reinterpret_cast<unsigned short *>(d)[i] = (unsigned short)v;
+    }
+}
+
+template <class F>
+float time_ms(F &&fn, cudaStream_t s, int reps)
+{
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    fn();  // warm-up
+    cudaEventRecord(a, s);
+    for (int r = 0; r < reps; ++r) fn();
+    cudaEventRecord(b, s);
+    cudaEventSynchronize(b);
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    return cudaGetLastError() == cudaSuccess ? ms / reps : 1e30f;
+}
+
+}  // namespace
+}  // namespace ecc
+
+using namespace ecc;
+
+void ecc_plan_s::autotune()
+{
+    // explicit overrides (benchmark sweeps): ECC_TILE3D = 61 | 62 | 42 | 31
+    if (const char *t = std::getenv("ECC_TILE3D")) {
+        const int v = std::atoi(t);
+        tuned[1] = tuned[3] = v;
+    }
+    if (d.flags & ECC_FLAG_NO_AUTOTUNE) return;
+    if (const char *e = std::getenv("ECC_TUNE"))
+        if (!std::strcmp(e, "off")) return;
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) return;
+    std::ostringstream k;
+    for (const char *c = prop.name; *c; ++c) k << (*c == ' ' ? '_' : *c);
+    k << '|' << num_sms << '|' << (d.dtype == ECC_U16 ? "u16" : "u8") << '|' << d.complex_mode;
+    const std::string key = k.str();
+    const int key3d = 1 | (d.dtype == ECC_U16 ? 2 : 0);
+    const bool want_batch = d.max_images >= 2 && !(d.flags & ECC_FLAG_BATCH_PER_IMAGE);
+    bool need3d = true, needb = want_batch;
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        load_cache();
+        auto it = g_tuned.find(key + "|3d");
+        if (std::getenv("ECC_TILE3D")) {
+            need3d = false;
+        } else if (it != g_tuned.end()) {
+            tuned[key3d] = it->second.a;
+            need3d = false;
+        }
+        it = g_tuned.find(key + "|batch");
+        if (want_batch && it != g_tuned.end()) {
+            tuned_batch[0] = it->second.a;
+            tuned_batch[1] = it->second.b;
+            needb = false;
+        }
+    }
+    if (!need3d && !needb) return;
+    const int es = d.dtype == ECC_U16 ? 2 : 1;
+    cudaStream_t s = nullptr;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return;
+    const bool range = !(d.flags & ECC_FLAG_NO_RANGE_CHECK);
+    if (need3d) {
+        // 3D single-image kernel on a synthetic 352x150x128 volume
+        const int nx = 352, ny = 150, nz = 128;
+        const int64_t n = (int64_t)nx * ny * nz;
+        unsigned char *buf = nullptr;
+        Choice c;
+        if (cudaMalloc(&buf, n * es) == cudaSuccess) {
+            synth_fill<<<1024, 256, 0, s>>>(buf, n, es, nx, ny, d.lo, d.hi);
+            Geom g{buf, nz, ny, nx, (int64_t)nx * es, (int64_t)nx * ny * es, 3, es};
+            HistDst h{acc, d.lo, nbins};
+            float best = 1e30f;
+            for (int tp : {62, 61, 42, 31}) {
+                const float ms = time_ms(
+                    [&] { launch_bitslice(g, 0, nz, h, d.complex_mode, range, status, sched, num_sms, tp, s); }, s,
+                    5);
+                if (ms < best) {
+                    best = ms;
+                    c.a = tp;
+                }
+            }
+            cudaStreamSynchronize(s);
+            cudaFree(buf);
+        }
+        cudaMemsetAsync(acc, 0, sizeof(unsigned long long) * nbins, s);
+        cudaMemsetAsync(status, 0, sizeof(unsigned int), s);
+        cudaStreamSynchronize(s);
+        cudaGetLastError();
+        tuned[key3d] = c.a;
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tuned[key + "|3d"] = c;
+        save_choice(key + "|3d", c);
+    }
+    if (needb) {
+        // batched kernel on an uneven synthetic batch (2D and 3D images in one buffer)
+        std::vector<ecc_image> imgs;
+        std::vector<int64_t> offs;
+        int64_t total = 0;
+        const int n2 = d.max_images >= 48 ? 40 : d.max_images / 2 + 1;
+        const int n3 = d.max_images - n2 >= 8 ? 8 : d.max_images - n2;
+        for (int i = 0; i < n2 + n3; ++i) {
+            ecc_image im{};
+            im.dtype = d.dtype;
+            if (i < n2) {
+                im.ndim = 2;
+                im.dims[0] = 100 + 37 * i % 400;
+                im.dims[1] = 150 + 53 * i % 500;
+                offs.push_back(total);
+                total += im.dims[0] * im.dims[1];
+            } else {
+                const int64_t sd = 48 + 16 * ((i - n2) % 5);
+                im.ndim = 3;
+                im.dims[0] = im.dims[1] = im.dims[2] = sd;
+                offs.push_back(total);
+                total += sd * sd * sd;
+            }
+            imgs.push_back(im);
+        }
+        unsigned char *buf = nullptr;
+        long long *out = nullptr;
+        Choice c;
+        if (total <= d.max_voxels && cudaMalloc(&buf, total * es) == cudaSuccess &&
+            cudaMalloc(&out, sizeof(long long) * nbins * imgs.size()) == cudaSuccess) {
+            synth_fill<<<1024, 256, 0, s>>>(buf, total, es, 97, 89, d.lo, d.hi);
+            for (size_t i = 0; i < imgs.size(); ++i) imgs[i].data = buf + offs[i] * es;
+            float best = 1e30f;
+            for (int c2 : {16, 32, 64})
+                for (int c3 : {8, 16, 32}) {
+                    release_batch(this);
+                    tuned_batch[0] = c2;
+                    tuned_batch[1] = c3;
+                    const float ms = time_ms(
+                        [&] {
+                            ecc_compute_batch(this, (int32_t)imgs.size(), imgs.data(), reinterpret_cast<int64_t *>(out),
+                                              s);
+                        },
+                        s, 3);
+                    if (ms < best) {
+                        best = ms;
+                        c.a = c2;
+                        c.b = c3;
+                    }
+                }
+            release_batch(this);
+            cudaStreamSynchronize(s);
+        }
+        if (out) cudaFree(out);
+        if (buf) cudaFree(buf);
+        cudaMemsetAsync(status, 0, sizeof(unsigned int), s);
+        cudaStreamSynchronize(s);
+        cudaGetLastError();
+        tuned_batch[0] = c.a;
+        tuned_batch[1] = c.b;
+        if (c.a) {
+            std::lock_guard<std::mutex> lk(g_tune_mu);
+            g_tuned[key + "|batch"] = c;
+            save_choice(key + "|batch", c);
+        }
+    }
+    cudaStreamDestroy(s);
+}

@@ -111,24 +111,21 @@ __device__ __forceinline__ void planes_from_words(const uint32_t *w, int sh, uin
 
 // ------------------------------------------------------------------ 3D
 
-// One plane's part of a lane: row y as planes P, row y+1 (the next lane's P)
-// as U, and row y shifted by one voxel each way (Pp[x] = P[x+1], Pm[x] = P[x-1]).
+// One plane's part of a lane: row y as planes P and row y+1 (the next
+// lane's P) as U.  The one-voxel shifts of P are recomputed where needed
+// (multiplies on the otherwise idle FMA pipe) rather than kept, to save
+// registers.
 template <int K>
 struct Rows3 {
-    uint32_t P[K], U[K], Pp[K], Pm[K];
-    int off;  // loader bookkeeping (byte offset of the window in a staged row)
+    uint32_t P[K], U[K];
 };
 
-// Fill U and the shifts of a freshly loaded P.  Warp-collective.
+// Fill U of a freshly loaded P.  Warp-collective.
 template <int K>
 __device__ __forceinline__ void complete_rows(Rows3<K> &r)
 {
 #pragma unroll
-    for (int k = 0; k < K; ++k) {
-        r.U[k] = from_next_lane(r.P[k]);
-        r.Pp[k] = shr1(r.P[k]);
-        r.Pm[k] = shl1(r.P[k]);
-    }
+    for (int k = 0; k < K; ++k) r.U[k] = from_next_lane(r.P[k]);
 }
 
 template <int K, bool TOP>
@@ -164,22 +161,29 @@ struct Walk3d {
     {
         // plane z against plane z+1 (z earlier): H0[d][x] = A[x-d] vs B[x],
         // Hp[d][x] = A[x-d] vs Bu[x], K2[d][x] = Au[x] vs B[x+d]
-        uint32_t H0[3], Hp[3], K2[3];
-        H0[0] = beats_later<K, TOP>(a.Pp, b.P);
-        H0[1] = beats_later<K, TOP>(a.P, b.P);
-        H0[2] = beats_later<K, TOP>(a.Pm, b.P);
-        Hp[0] = beats_later<K, TOP>(a.Pp, b.U);
-        Hp[1] = beats_later<K, TOP>(a.P, b.U);
-        Hp[2] = beats_later<K, TOP>(a.Pm, b.U);
-        K2[0] = beats_later<K, TOP>(a.U, b.Pm);
-        K2[1] = beats_later<K, TOP>(a.U, b.P);
-        K2[2] = beats_later<K, TOP>(a.U, b.Pp);
-        // in-plane pairs of plane z+1: E[x] = B[x-1] vs B[x], F[d][x] = B[x-d] vs Bu[x]
-        const uint32_t E = beats_later<K, TOP>(b.Pm, b.P);
-        uint32_t F[3];
-        F[0] = beats_later<K, TOP>(b.Pp, b.U);
-        F[1] = beats_later<K, TOP>(b.P, b.U);
-        F[2] = beats_later<K, TOP>(b.Pm, b.U);
+        uint32_t H0[3], Hp[3], K2[3], E, F[3];
+        {
+            uint32_t Ap[K], Am[K];
+            shifted<K>(a.P, Ap, Am);
+            H0[0] = beats_later<K, TOP>(Ap, b.P);
+            H0[1] = beats_later<K, TOP>(a.P, b.P);
+            H0[2] = beats_later<K, TOP>(Am, b.P);
+            Hp[0] = beats_later<K, TOP>(Ap, b.U);
+            Hp[1] = beats_later<K, TOP>(a.P, b.U);
+            Hp[2] = beats_later<K, TOP>(Am, b.U);
+        }
+        {
+            uint32_t Bp[K], Bm[K];
+            shifted<K>(b.P, Bp, Bm);
+            K2[0] = beats_later<K, TOP>(a.U, Bm);
+            K2[1] = beats_later<K, TOP>(a.U, b.P);
+            K2[2] = beats_later<K, TOP>(a.U, Bp);
+            // in-plane pairs of plane z+1: E[x] = B[x-1] vs B[x], F[d][x] = B[x-d] vs Bu[x]
+            E = beats_later<K, TOP>(Bm, b.P);
+            F[0] = beats_later<K, TOP>(Bp, b.U);
+            F[1] = beats_later<K, TOP>(b.P, b.U);
+            F[2] = beats_later<K, TOP>(Bm, b.U);
+        }
         uint32_t Hp_dn[3], K2_dn[3], F_dn[3];
 #pragma unroll
         for (int d = 0; d < 3; ++d) {

@@ -205,3 +205,16 @@ def test_config1_matches_golden():
                           dtype=np.int64)
         for kernel in KERNELS:
             assert np.array_equal(_run(_gpu(img), 0, 255, mode, kernel), want)
+
+
+@pytest.mark.parametrize("tile", ["61", "62", "42", "31"])
+def test_every_3d_tile_variant(tile, monkeypatch):
+    """Each tile shape / histogram-copy variant the autotuner may pick is exact."""
+    monkeypatch.setenv("ECC_TILE3D", tile)
+    rng = np.random.default_rng(int(tile))
+    for shape, dt, levels in [((37, 70, 208), np.uint8, 256), ((21, 45, 96), np.uint8, 4),
+                              ((19, 33, 136), np.uint16, 65536)]:
+        img = rng.integers(0, levels, size=shape).astype(dt)
+        hi = 255 if dt == np.uint8 else 65535
+        for mode in MODES:
+            assert np.array_equal(_run(_gpu(img), 0, hi, mode), _expect(img, 0, hi, mode)), (tile, shape, mode)
