@@ -194,6 +194,16 @@ int32_t ecc_plan_last_launches(ecc_plan_t plan);
  * record.  Errors: ECC_E_INVALID (flag not set), ECC_E_CUDA. */
 ecc_status ecc_plan_kernel_time(ecc_plan_t plan, double *ms, int64_t *launches);
 
+/* Failure-detection self-test: launches one warp that waits on a device flag
+ * nothing sets (the scan's look-back pattern) and then on an mbarrier nothing
+ * arrives on (the TMA ring's pattern), each bounded by limit_us; every such
+ * wait in the library gives up the same way and reports ECC_E_TIMEOUT through
+ * the device status word instead of hanging.  gave_up[0..1] = 1 for each wait
+ * that ran out.  Expected result: ECC_E_TIMEOUT with both set; the CUDA
+ * context stays usable.  The paper has no counterpart.
+ * Errors: ECC_E_INVALID (limit_us outside [1, 1e7]), ECC_E_CUDA. */
+ecc_status ecc_selftest_wait_timeout(int64_t limit_us, int32_t *gave_up, void *stream);
+
 /* Thread-local message describing the last failure of this thread. */
 const char *ecc_last_error(void);
 

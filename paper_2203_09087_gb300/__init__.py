@@ -47,6 +47,7 @@ from ._binding import (  # noqa: F401
     ecc_plan_kernel_time,
     ecc_plan_last_launches,
     ecc_plan_nbins,
+    ecc_selftest_wait_timeout,
     ecc_server_create,
     ecc_server_destroy,
     ecc_server_stats,

@@ -64,6 +64,7 @@ _SIGNATURES = {
     "ecc_status_get": (ctypes.c_int, [_VP, _VP]),
     "ecc_plan_kernel_time": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_I64)]),
     "ecc_last_error": (ctypes.c_char_p, []),
+    "ecc_selftest_wait_timeout": (ctypes.c_int, [_I64, ctypes.POINTER(ctypes.c_int32), _VP]),
     "ecc_server_create": (ctypes.c_int, [ctypes.POINTER(_VP), ctypes.POINTER(EccServerDesc)]),
     "ecc_submit": (ctypes.c_int, [_VP, ctypes.POINTER(EccImage), _I32, _I32, _I32, _I32, _VP, DONE_FN, _VP,
                                   ctypes.POINTER(_U64)]),
@@ -294,6 +295,15 @@ def ecc_compute_noalloc(image, lo: int = 0, hi: int | None = None, complex_mode:
     _check(library().ecc_compute_noalloc(ctypes.byref(d), int(lo), int(hi), int(complex_mode), int(flags),
                                          out.data_ptr(), vptr, _stream_handle(stream)))
     return out
+
+
+def ecc_selftest_wait_timeout(limit_us: int = 50_000, stream=None):
+    """Run the bounded-wait self-test; returns (status, [flag wait gave up, mbarrier wait gave up])."""
+    gave = (ctypes.c_int32 * 2)()
+    st = library().ecc_selftest_wait_timeout(int(limit_us), gave, _stream_handle(stream))
+    if st not in (ECC_OK, ECC_E_TIMEOUT):
+        _check(st)
+    return st, [int(gave[0]), int(gave[1])]
 
 
 def ecc_status_get(plan: Plan, stream=None) -> int:

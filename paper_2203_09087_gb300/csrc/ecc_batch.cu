@@ -191,11 +191,10 @@ __device__ void run_tile(const BatchArgs &a, const BatchImage &im, long long loc
             if (y1 + 1 <= ye) sh = fetch(y1 + 1, wn);
             wk.step(B, y1 < im.ny, y1 - 1 >= 0, y1 - 1 >= yb, out_x,
                     [&](uint32_t m, const uint32_t *Q, const uint32_t *F, const uint32_t *A) {
-                        while (m) {
-                            const int i = __ffs(m) - 1;
-                            m &= m - 1;
-                            em.add(bs::bits_at<K>(A, i), 1 + bs::bits_at<3>(Q, i) - bs::bits_at<3>(F, i));
-                        }
+                        walk::emit_aggregated(
+                            m, [&](int i) { return bs::bits_at<K>(A, i); },
+                            [&](int i) { return 1 + bs::bits_at<3>(Q, i) - bs::bits_at<3>(F, i); }, em.hist, em.acc,
+                            em.lo, em.nbins, em.range_check, em.status);
                     });
         }
     } else {
@@ -224,14 +223,11 @@ __device__ void run_tile(const BatchArgs &a, const BatchImage &im, long long loc
         const bool inner_xy = xw >= 0 && xw + 32 <= im.nx && y0 >= 0 && y0 + 31 < im.ny;
         walk::Walk3d<K, TOP> wk;
         wk.begin(xex, y - 1 >= 0 && y - 1 < im.ny, y + 1 >= 0 && y + 1 < im.ny);
-        auto emit = [&](uint32_t m, const uint32_t *S, const uint32_t *N, const uint32_t *A) {
-            while (m) {
-                const int i = __ffs(m) - 1;
-                m &= m - 1;
-                int kap = 1 + bs::bits_at<4>(S, i) - bs::bits_at<4>(N, i);
-                if (TOP) kap = -kap;  // (-1)^d, d = 3
-                em.add(bs::bits_at<K>(A, i), kap);
-            }
+        auto emit = [&](uint32_t m, const uint32_t *Tc, const uint32_t *A) {
+            walk::emit_aggregated(
+                m, [&](int i) { return bs::bits_at<K>(A, i); },
+                [&](int i) { return TOP ? 13 - bs::bits_at<5>(Tc, i) : bs::bits_at<5>(Tc, i) - 13; }, em.hist, em.acc,
+                em.lo, em.nbins, em.range_check, em.status);
         };
         uint32_t wn[NWORDS + 1];
         walk::Rows3<K> r0, r1;
@@ -266,7 +262,7 @@ __device__ void run_tile(const BatchArgs &a, const BatchImage &im, long long loc
 }
 
 template <int K, bool TOP>
-__global__ void __launch_bounds__(kBatchWarps * 32) batch_kernel(BatchArgs a)
+__global__ void __launch_bounds__(kBatchWarps * 32, 1) batch_kernel(BatchArgs a)
 {
     extern __shared__ __align__(16) int bhist[];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -345,8 +341,7 @@ cudaError_t capture_graph(ecc_plan_s *p, BatchState *b)
     if (per_sm < 1) return cudaErrorNotSupported;
     b->persistent_ctas = p->num_sms * per_sm;
 
-    static BatchArgs args;  // copied into the graph at capture
-    args = BatchArgs{};
+    BatchArgs args{};  // the kernel nodes copy their arguments at creation
     args.hdr = reinterpret_cast<const BatchHeader *>(b->d_desc);
     args.img = reinterpret_cast<const BatchImage *>(b->d_desc + sizeof(BatchHeader));
     args.start = b->d_start;

@@ -38,6 +38,7 @@
 
 #include "ecc_bitslice.cuh"
 #include "ecc_internal.h"
+#include "ecc_sync.cuh"
 #include "ecc_walk.cuh"
 
 namespace ecc {
@@ -77,50 +78,13 @@ struct Bs3dArgs {
     unsigned int *status;
 };
 
-// ----------------------------------------------------------------- PTX helpers
+// ----------------------------------------------------------------- TMA
 
-__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ unsigned long long globaltimer()
-{
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
-{
-    uint32_t done;
-    asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-        : "=r"(done)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return done != 0;
-}
-
-// Bounded wait: false after kSpinLimitNs without completion.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
-{
-    if (mbar_try_wait(bar, parity)) return true;
-    const unsigned long long t0 = globaltimer();
-    for (;;) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if (globaltimer() - t0 > kSpinLimitNs) return false;
-    }
-}
-
+using sync::mbar_arrive;
+using sync::mbar_expect_tx;
+using sync::mbar_init;
+using sync::mbar_wait;
+using sync::smem_u32;
 __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int x, int y, int z, uint64_t *bar)
 {
     asm volatile(
@@ -147,12 +111,18 @@ __device__ __forceinline__ void load_window(const unsigned char *row, int off, u
     }
     uint32_t r[C::WORDS];
     const int wsh = (sh & 3) * 8;
-    // the word offset is uniform across the warp (all lanes read the same columns)
+    const uint32_t m = bs::kPow2[(32 - wsh) & 31];  // unused when wsh == 0
+    // the word offset is uniform across the warp (all lanes read the same
+    // columns); the byte shift is done as two multiplies on the FMA pipe
     switch (sh >> 2) {
 #define ECC_WIN(W)                                                                     \
     case W:                                                                            \
-        _Pragma("unroll") for (int i = 0; i < C::WORDS; ++i) r[i] =                    \
-            __funnelshift_r(v[i + W], v[i + W + 1], wsh);                              \
+        if (wsh == 0) {                                                                \
+            _Pragma("unroll") for (int i = 0; i < C::WORDS; ++i) r[i] = v[i + W];      \
+        } else {                                                                       \
+            _Pragma("unroll") for (int i = 0; i < C::WORDS; ++i) r[i] =                \
+                v[i + W + 1] * m + __umulhi(v[i + W], m);                              \
+        }                                                                              \
         break;
         ECC_WIN(0)
         ECC_WIN(1)
@@ -164,11 +134,6 @@ __device__ __forceinline__ void load_window(const unsigned char *row, int off, u
         bs::transpose_u8(r, planes);
     else
         bs::transpose_u16(r, planes);
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
-{
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
 // NW compute warps and one producer warp.  Stage s of the ring has a "full"
@@ -327,22 +292,11 @@ __global__ void __launch_bounds__((NW + 1) * 32, bs3d_min_blocks<T, NW>())
             const bool inner_xy = xw >= 0 && xw + 32 <= a.nx && y0 >= 0 && y0 + 31 < a.ny;
             walk::Walk3d<K, TOP> wk;
             wk.begin(xex, y - 1 >= 0 && y - 1 < a.ny, y + 1 >= 0 && y + 1 < a.ny);
-            auto emit = [&](uint32_t m, const uint32_t *Sq, const uint32_t *Nc, const uint32_t *A) {
-                while (m) {
-                    const int i = __ffs(m) - 1;
-                    m &= m - 1;
-                    int kap = 1 + bs::bits_at<4>(Sq, i) - bs::bits_at<4>(Nc, i);
-                    if (TOP) kap = -kap;  // (-1)^d, d = 3
-                    const int bin = bs::bits_at<K>(A, i) - a.h.lo;
-                    if (a.range_check && (unsigned)bin >= (unsigned)a.h.nbins) {
-                        atomicOr(a.status, DEV_RANGE);
-                        continue;
-                    }
-                    if (a.smem_hist)
-                        atomicAdd(&my_hist[bin], kap);
-                    else
-                        atomicAdd(a.h.acc + bin, (unsigned long long)(long long)kap);
-                }
+            auto emit = [&](uint32_t m, const uint32_t *Tc, const uint32_t *A) {
+                walk::emit_aggregated(
+                    m, [&](int i) { return bs::bits_at<K>(A, i); },
+                    [&](int i) { return TOP ? 13 - bs::bits_at<5>(Tc, i) : bs::bits_at<5>(Tc, i) - 13; },
+                    a.smem_hist ? my_hist : nullptr, a.h.acc, a.h.lo, a.h.nbins, a.range_check, a.status);
             };
             walk::Rows3<K> r0, r1;
             fetch(r0);  // plane zb-1 (its full barrier already passed)
@@ -451,20 +405,10 @@ __global__ void __launch_bounds__(kWarps2d * 32) bs2d_kernel(const Bs2dArgs a)
             return walk::load_row_words<K>(a.data + yy * a.pitch, row_bytes, first, w);
         };
         auto emit = [&](uint32_t m, const uint32_t *Q, const uint32_t *F, const uint32_t *A) {
-            while (m) {
-                const int i = __ffs(m) - 1;
-                m &= m - 1;
-                const int kap = 1 + bs::bits_at<3>(Q, i) - bs::bits_at<3>(F, i);  // (-1)^2 = +1
-                const int bin = bs::bits_at<K>(A, i) - a.h.lo;
-                if (a.range_check && (unsigned)bin >= (unsigned)a.h.nbins) {
-                    atomicOr(a.status, DEV_RANGE);
-                    continue;
-                }
-                if (a.smem_hist)
-                    atomicAdd(&my_hist[bin], kap);
-                else
-                    atomicAdd(a.h.acc + bin, (unsigned long long)(long long)kap);
-            }
+            walk::emit_aggregated(
+                m, [&](int i) { return bs::bits_at<K>(A, i); },
+                [&](int i) { return 1 + bs::bits_at<3>(Q, i) - bs::bits_at<3>(F, i); },  // (-1)^2 = +1
+                a.smem_hist ? my_hist : nullptr, a.h.acc, a.h.lo, a.h.nbins, a.range_check, a.status);
         };
         uint32_t wn[K + 1], P[K];
         int sh = fetch(yb - 1, wn);

@@ -20,6 +20,38 @@
 namespace ecc {
 namespace bs {
 
+#if defined(__CUDACC__)
+// Powers of two in constant memory.  A shift written as a multiply by one
+// of them issues on the FMA pipe (x << d = x * 2^d; x >> d = high word of
+// x * 2^(32-d)); because the factor is not a compile-time constant the
+// compiler cannot turn it back into a shift on the integer ALU pipe, which
+// the bit logic of the stencil already saturates.
+static __constant__ uint32_t kPow2[33] = {
+    1u << 0,  1u << 1,  1u << 2,  1u << 3,  1u << 4,  1u << 5,  1u << 6,  1u << 7,  1u << 8,
+    1u << 9,  1u << 10, 1u << 11, 1u << 12, 1u << 13, 1u << 14, 1u << 15, 1u << 16, 1u << 17,
+    1u << 18, 1u << 19, 1u << 20, 1u << 21, 1u << 22, 1u << 23, 1u << 24, 1u << 25, 1u << 26,
+    1u << 27, 1u << 28, 1u << 29, 1u << 30, 1u << 31, 0u};
+#endif
+
+// x << d and x >> d for 0 < d < 32 (multiplies on the FMA pipe on the device)
+BS_HD uint32_t shl_m(uint32_t x, int d)
+{
+#if defined(__CUDA_ARCH__)
+    return x * kPow2[d];
+#else
+    return x << d;
+#endif
+}
+
+BS_HD uint32_t shr_m(uint32_t x, int d)
+{
+#if defined(__CUDA_ARCH__)
+    return __umulhi(x, kPow2[32 - d]);
+#else
+    return x >> d;
+#endif
+}
+
 // Byte permute: result byte i = byte (s >> 4i) & 7 of the 8 bytes {a, b}.
 BS_HD uint32_t byte_perm(uint32_t a, uint32_t b, uint32_t s)
 {
@@ -39,8 +71,8 @@ BS_HD uint32_t byte_perm(uint32_t a, uint32_t b, uint32_t s)
 BS_HD void swap_bit(uint32_t &lo, uint32_t &hi, int d, uint32_t M)
 {
     const uint32_t a = lo, b = hi;
-    lo = (a & ~M) | ((b << d) & M);
-    hi = ((a >> d) & ~M) | (b & M);
+    lo = (a & ~M) | (shl_m(b, d) & M);
+    hi = (shr_m(a, d) & ~M) | (b & M);
 }
 
 // 32 uint8 voxels in r[0..7] (little-endian: byte j of r[q] is voxel 4q+j)
@@ -114,45 +146,6 @@ BS_HD void half_add(uint32_t a, uint32_t b, uint32_t &s, uint32_t &carry)
     carry = a & b;
 }
 
-// Per-voxel count of 12 one-bit inputs as four bit planes (max 12).
-BS_HD void count12(const uint32_t x[12], uint32_t o[4])
-{
-    uint32_t a[4], b[4];
-    full_add(x[0], x[1], x[2], a[0], b[0]);
-    full_add(x[3], x[4], x[5], a[1], b[1]);
-    full_add(x[6], x[7], x[8], a[2], b[2]);
-    full_add(x[9], x[10], x[11], a[3], b[3]);
-    uint32_t c1, d2, e2;
-    full_add(a[0], a[1], a[2], c1, d2);
-    half_add(c1, a[3], o[0], e2);                  // weight 1 done
-    uint32_t f2, g4, f2b, g4b, h4;
-    full_add(b[0], b[1], b[2], f2, g4);
-    full_add(b[3], d2, e2, f2b, g4b);
-    half_add(f2, f2b, o[1], h4);                   // weight 2 done
-    full_add(g4, g4b, h4, o[2], o[3]);             // weights 4 and 8
-}
-
-// Per-voxel count of 14 one-bit inputs as four bit planes (max 14).
-BS_HD void count14(const uint32_t x[14], uint32_t o[4])
-{
-    uint32_t a[4], b[4];
-    full_add(x[0], x[1], x[2], a[0], b[0]);
-    full_add(x[3], x[4], x[5], a[1], b[1]);
-    full_add(x[6], x[7], x[8], a[2], b[2]);
-    full_add(x[9], x[10], x[11], a[3], b[3]);
-    uint32_t s1, c1, s2, c2, c3;
-    full_add(a[0], a[1], a[2], s1, c1);
-    full_add(a[3], x[12], x[13], s2, c2);
-    half_add(s1, s2, o[0], c3);                    // weight 1 done; weight 2: b[0..3], c1, c2, c3
-    uint32_t t1, u1, t2, u2, u3;
-    full_add(b[0], b[1], b[2], t1, u1);
-    full_add(b[3], c1, c2, t2, u2);
-    uint32_t t3;
-    full_add(t1, t2, c3, o[1], u3);                // weight 2 done; weight 4: u1, u2, u3
-    full_add(u1, u2, u3, o[2], o[3]);
-    (void)t3;
-}
-
 // Per-voxel count of 4 one-bit inputs as three bit planes (max 4).
 BS_HD void count4(uint32_t a, uint32_t b, uint32_t c, uint32_t d, uint32_t o[3])
 {
@@ -160,19 +153,6 @@ BS_HD void count4(uint32_t a, uint32_t b, uint32_t c, uint32_t d, uint32_t o[3])
     full_add(a, b, c, s, c1);
     half_add(s, d, o[0], c2);
     half_add(c1, c2, o[1], o[2]);
-}
-
-// Mask of voxels where the 4-bit value x + 1 differs from the 4-bit value n.
-BS_HD uint32_t plus_one_differs(const uint32_t x[4], const uint32_t n[4])
-{
-    const uint32_t p0 = ~x[0];
-    const uint32_t c0 = x[0];
-    const uint32_t p1 = x[1] ^ c0;
-    const uint32_t c1 = x[1] & c0;
-    const uint32_t p2 = x[2] ^ c1;
-    const uint32_t c2 = x[2] & c1;
-    const uint32_t p3 = x[3] ^ c2;
-    return (p0 ^ n[0]) | (p1 ^ n[1]) | (p2 ^ n[2]) | (p3 ^ n[3]);
 }
 
 // Value of a bit-sliced field at bit i.
@@ -193,14 +173,48 @@ BS_HD int bits_at(const uint32_t *x, int i)
 // voxel's rival for any cell they share).
 //
 // kappa = sum over cells containing the voxel that it introduces of
-// (-1)^dim = 1 - faces + squares - cubes.  Returns the nonzero mask and the
-// bit planes of S = squares and N = faces + cubes (kappa = 1 + S - N).
-BS_HD uint32_t kappa3d(const uint32_t w[3][3][3], uint32_t S[4], uint32_t N[4])
+// (-1)^dim = 1 - F + S - C with F faces (6), S squares (12), C cubes (8).
+// Equivalently kappa = T - 13 where T counts the 26 one-bit terms
+// {squares} + {not face} + {not cube} (since 1 - F - C = (6 - F) + (8 - C) - 13).
+// Returns the nonzero mask (T != 13) and the five bit planes of T.
+
+// Per-voxel count of 26 one-bit inputs as five bit planes (max 26).
+BS_HD void count26(const uint32_t x[26], uint32_t o[5])
+{
+    uint32_t s[8], c[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) full_add(x[3 * i], x[3 * i + 1], x[3 * i + 2], s[i], c[i]);
+    // weight 1: s[0..7], x[24], x[25]
+    uint32_t a0, a1, a2, d0, d1, d2, b0, e0, e1;
+    full_add(s[0], s[1], s[2], a0, d0);
+    full_add(s[3], s[4], s[5], a1, d1);
+    full_add(s[6], s[7], x[24], a2, d2);
+    full_add(a0, a1, a2, b0, e0);
+    half_add(b0, x[25], o[0], e1);
+    // weight 2: c[0..7], d0, d1, d2, e0, e1 (13 terms)
+    uint32_t f[4], g[4];
+    full_add(c[0], c[1], c[2], f[0], g[0]);
+    full_add(c[3], c[4], c[5], f[1], g[1]);
+    full_add(c[6], c[7], d0, f[2], g[2]);
+    full_add(d1, d2, e0, f[3], g[3]);
+    uint32_t h0, k0, k1;
+    full_add(f[0], f[1], f[2], h0, k0);
+    full_add(f[3], e1, h0, o[1], k1);
+    // weight 4: g[0..3], k0, k1 (6 terms)
+    uint32_t m0, n0, m1, n1, n2;
+    full_add(g[0], g[1], g[2], m0, n0);
+    full_add(g[3], k0, k1, m1, n1);
+    half_add(m0, m1, o[2], n2);
+    // weight 8: n0, n1, n2
+    full_add(n0, n1, n2, o[3], o[4]);
+}
+
+BS_HD uint32_t kappa3d(const uint32_t w[3][3][3], uint32_t T[5])
 {
     const uint32_t ex[2] = {w[1][1][0], w[1][1][2]};
     const uint32_t ey[2] = {w[1][0][1], w[1][2][1]};
     const uint32_t ez[2] = {w[0][1][1], w[2][1][1]};
-    uint32_t sq[12];
+    uint32_t t[26];
     uint32_t sxy[2][2], sxz[2][2], syz[2][2];
 #pragma unroll
     for (int a = 0; a < 2; ++a)
@@ -209,27 +223,26 @@ BS_HD uint32_t kappa3d(const uint32_t w[3][3][3], uint32_t S[4], uint32_t N[4])
             sxy[a][b] = ey[a] & ex[b] & w[1][2 * a][2 * b];   // y side a, x side b
             sxz[a][b] = ez[a] & ex[b] & w[2 * a][1][2 * b];   // z side a, x side b
             syz[a][b] = ez[a] & ey[b] & w[2 * a][2 * b][1];   // z side a, y side b
-            sq[0 + 2 * a + b] = sxy[a][b];
-            sq[4 + 2 * a + b] = sxz[a][b];
-            sq[8 + 2 * a + b] = syz[a][b];
+            t[0 + 2 * a + b] = sxy[a][b];
+            t[4 + 2 * a + b] = sxz[a][b];
+            t[8 + 2 * a + b] = syz[a][b];
         }
-    uint32_t n[14];
-    n[0] = ex[0];
-    n[1] = ex[1];
-    n[2] = ey[0];
-    n[3] = ey[1];
-    n[4] = ez[0];
-    n[5] = ez[1];
+    t[12] = ~ex[0];
+    t[13] = ~ex[1];
+    t[14] = ~ey[0];
+    t[15] = ~ey[1];
+    t[16] = ~ez[0];
+    t[17] = ~ez[1];
 #pragma unroll
     for (int c = 0; c < 2; ++c)
 #pragma unroll
         for (int b = 0; b < 2; ++b)
 #pragma unroll
             for (int a = 0; a < 2; ++a)   // cube on z side c, y side b, x side a
-                n[6 + 4 * c + 2 * b + a] = sxy[b][a] & sxz[c][a] & syz[c][b] & w[2 * c][2 * b][2 * a];
-    count12(sq, S);
-    count14(n, N);
-    return plus_one_differs(S, N);
+                t[18 + 4 * c + 2 * b + a] = ~(sxy[b][a] & sxz[c][a] & syz[c][b] & w[2 * c][2 * b][2 * a]);
+    count26(t, T);
+    // T == 13 = 0b01101
+    return ~(T[0] & ~T[1] & T[2] & T[3] & ~T[4]);
 }
 
 // 2D: w[dy+1][dx+1]; kappa = 1 - faces + squares.  Returns the nonzero mask

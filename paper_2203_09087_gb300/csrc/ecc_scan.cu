@@ -12,16 +12,10 @@
 // out if asked and zeroes the accumulator, and the last tile resets the
 // look-back state, so the workspace is clean for the next call.
 #include "ecc_internal.h"
+#include "ecc_sync.cuh"
 
 namespace ecc {
 namespace {
-
-__device__ __forceinline__ unsigned long long globaltimer()
-{
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
 
 // Segmented-scan operator on (flag, value): a then b.
 __device__ __forceinline__ void seg_combine(bool af, long long av, bool &bf, long long &bv)
@@ -142,12 +136,8 @@ __global__ void __launch_bounds__(kScanThreads) scan_kernel(ScanArgs a)
         const bool needs_carry = (tile * kScanTile) % a.nbins != 0 && tile * kScanTile < a.n;
         if (needs_carry) {
             int64_t j = tile - 1;
-            const unsigned long long t0 = globaltimer();
             while (j >= 0) {
-                int s;
-                while ((s = st[j]) == 0) {
-                    if (globaltimer() - t0 > kSpinLimitNs) break;
-                }
+                const int s = sync::flag_wait(st + j);
                 if (s == 0) {
                     atomicOr(a.status, DEV_TIMEOUT);
                     break;

@@ -108,6 +108,17 @@ struct ecc_server_s {
 namespace ecc {
 namespace {
 
+// Jobs worth a launch of their own: 3D volumes of at least 2^23 voxels
+// whose rows the TMA-staged kernel can load (16-byte aligned base and pitches).
+bool big_volume(const Job &j)
+{
+    const Geom &g = j.geom;
+    if (j.host_input)  // copied densely into a fresh (256-byte aligned) buffer
+        return g.ndim == 3 && j.voxels >= (int64_t(1) << 23) && (g.nx * g.esize) % 16 == 0;
+    return g.ndim == 3 && j.voxels >= (int64_t(1) << 23) && reinterpret_cast<uintptr_t>(g.data) % 16 == 0 &&
+           g.pitch_y % 16 == 0 && g.pitch_z % 16 == 0;
+}
+
 int64_t job_bytes(const Job &j)
 {
     const int64_t io = j.host_input ? j.voxels * j.geom.esize : 0;
@@ -164,6 +175,9 @@ void launch_batch(ecc_server_s *s, std::unique_lock<std::mutex> &lk, Slot &slot)
             ++it;
         }
     }
+    // large 3D volumes whose rows the TMA kernel can stage go last and run
+    // on the single-image kernel; everything else shares one batched launch
+    std::stable_partition(batch.begin(), batch.end(), [](const std::unique_ptr<Job> &j) { return !big_volume(*j); });
     slot.busy = true;
     lk.unlock();
 
@@ -200,9 +214,13 @@ void launch_batch(ecc_server_s *s, std::unique_lock<std::mutex> &lk, Slot &slot)
         }
     }
     const int32_t nb = k.hi - k.lo + 1;
-    if (st == ECC_OK)
-        st = ecc_compute_batch(plan, (int32_t)batch.size(), descs.data(), reinterpret_cast<int64_t *>(slot.d_ecc),
+    size_t n_small = 0;
+    while (n_small < batch.size() && !big_volume(*batch[n_small])) ++n_small;
+    if (st == ECC_OK && n_small > 0)
+        st = ecc_compute_batch(plan, (int32_t)n_small, descs.data(), reinterpret_cast<int64_t *>(slot.d_ecc),
                                slot.stream);
+    for (size_t i = n_small; i < batch.size() && st == ECC_OK; ++i)
+        st = ecc_compute(plan, &descs[i], reinterpret_cast<int64_t *>(slot.d_ecc + i * nb), nullptr, slot.stream);
     if (st == ECC_OK) {
         cudaError_t e = cudaMemcpyAsync(slot.h_ecc, slot.d_ecc, sizeof(long long) * nb * batch.size(),
                                         cudaMemcpyDeviceToHost, slot.stream);

@@ -20,6 +20,7 @@
 #include <stdint.h>
 
 #include "ecc_bitslice.cuh"
+#include "ecc_internal.h"
 
 namespace ecc {
 namespace walk {
@@ -27,11 +28,9 @@ namespace walk {
 __device__ __forceinline__ uint32_t from_next_lane(uint32_t v) { return __shfl_down_sync(0xffffffffu, v, 1); }
 __device__ __forceinline__ uint32_t from_prev_lane(uint32_t v) { return __shfl_up_sync(0xffffffffu, v, 1); }
 
-// One-bit shifts written as multiplies, so they can issue on the FMA pipe
-// (the integer logic of the stencil saturates the ALU pipe): x << 1 = x * 2,
-// x >> 1 = high word of x * 2^31.
-__device__ __forceinline__ uint32_t shl1(uint32_t x) { return x * 2u; }
-__device__ __forceinline__ uint32_t shr1(uint32_t x) { return __umulhi(x, 0x80000000u); }
+// One-bit shifts as multiplies on the FMA pipe (see bs::shl_m).
+__device__ __forceinline__ uint32_t shl1(uint32_t x) { return bs::shl_m(x, 1); }
+__device__ __forceinline__ uint32_t shr1(uint32_t x) { return bs::shr_m(x, 1); }
 
 // r[x] = m[x + dx]
 template <int DX>
@@ -101,12 +100,56 @@ __device__ __forceinline__ void planes_from_words(const uint32_t *w, int sh, uin
 {
     constexpr int NW = K;  // 32 voxels of K bits = K words
     uint32_t raw[NW];
+    if (sh == 0) {
 #pragma unroll
-    for (int i = 0; i < NW; ++i) raw[i] = __funnelshift_r(w[i], w[i + 1], sh);
+        for (int i = 0; i < NW; ++i) raw[i] = w[i];
+    } else {
+        // (w[i] >> sh) | (w[i+1] << (32 - sh)) as two multiplies (disjoint bits)
+        const uint32_t m = bs::kPow2[32 - sh];
+#pragma unroll
+        for (int i = 0; i < NW; ++i) raw[i] = w[i + 1] * m + __umulhi(w[i], m);
+    }
     if (K == 8)
         bs::transpose_u8(raw, planes);
     else
         bs::transpose_u16(raw, planes);
+}
+
+// ------------------------------------------------------------------ histogram
+
+// Adds the signed counts of the voxels in `m` (bit i: value val_at(i), count
+// kappa_at(i)) to the histogram, a warp at a time: each round every lane
+// with pending voxels offers one, lanes offering the same bin are grouped
+// with __match_any_sync, and one lane per group adds the group's sum
+// (__reduce_add_sync).  Shared bins when `hist` is set, else int64 global
+// bins.  Values outside [lo, lo + nbins) set DEV_RANGE and add nothing.
+// Warp-collective.
+template <class ValAt, class KappaAt>
+__device__ __forceinline__ void emit_aggregated(uint32_t m, ValAt &&val_at, KappaAt &&kappa_at, int *hist,
+                                                unsigned long long *acc, int lo, int nbins, bool range_check,
+                                                unsigned int *status)
+{
+    while (__any_sync(0xffffffffu, m != 0)) {
+        int bin = -1, kap = 0;
+        if (m) {
+            const int i = __ffs(m) - 1;
+            m &= m - 1;
+            kap = kappa_at(i);
+            bin = val_at(i) - lo;
+            if (range_check && (unsigned)bin >= (unsigned)nbins) {
+                atomicOr(status, DEV_RANGE);
+                bin = -1;
+            }
+        }
+        const unsigned peers = __match_any_sync(0xffffffffu, bin);
+        const int sum = __reduce_add_sync(peers, kap);
+        if (bin >= 0 && (__ffs(peers) - 1) == (int)(threadIdx.x & 31) && sum != 0) {
+            if (hist)
+                atomicAdd(&hist[bin], sum);
+            else
+                atomicAdd(acc + bin, (unsigned long long)(long long)sum);
+        }
+    }
 }
 
 // ------------------------------------------------------------------ 3D
@@ -153,8 +196,8 @@ struct Walk3d {
     // From plane z (rows a) to plane z+1 (rows b).  EDGE: apply the existence
     // masks (zp: plane z+1 exists, z_ok: plane z exists); without EDGE every
     // neighbour exists (interior tile).  When `emit_z` (warp-uniform), calls
-    // emit(mask, S, N, a.P) for plane z: output voxels with a nonzero count,
-    // count = 1 + S - N before the top-cell sign.  Warp-collective.
+    // emit(mask, T, a.P) for plane z: output voxels with a nonzero count,
+    // count = T - 13 before the top-cell sign.  Warp-collective.
     template <bool EDGE, class Emit>
     __device__ __forceinline__ void step(const Rows3<K> &a, const Rows3<K> &b, bool zp, bool z_ok, bool emit_z,
                                          uint32_t out_x, Emit &&emit)
@@ -221,9 +264,9 @@ struct Walk3d {
                 w[1][0][dx] = wym[dx];
                 w[1][2][dx] = wyp[dx];
             }
-            uint32_t S[4], N[4];
-            const uint32_t m = bs::kappa3d(w, S, N) & out_x;
-            emit(m, S, N, a.P);
+            uint32_t T[5];
+            const uint32_t m = bs::kappa3d(w, T) & out_x;
+            emit(m, T, a.P);
         }
         // wins of (z+1, y) over plane z (an earlier neighbour wins ties)
         Wm[1][0] = with_exist<TOP>(~H0[2], ez_m1 & eyy(1) & ex(0));

@@ -13,13 +13,15 @@ void h_transpose_u16(const uint32_t *r, uint32_t *p) { transpose_u16(r, p); }
 uint32_t h_ge8(const uint32_t *a, const uint32_t *b) { return ge<8>(a, b); }
 uint32_t h_ge16(const uint32_t *a, const uint32_t *b) { return ge<16>(a, b); }
 
-// w: 27 masks in [dz][dy][dx] order; writes S[4], N[4]; returns nonzero mask
-uint32_t h_kappa3d(const uint32_t *w27, uint32_t *S, uint32_t *N)
+// w: 27 masks in [dz][dy][dx] order; writes T[5] (kappa = T - 13); returns nonzero mask
+uint32_t h_kappa3d(const uint32_t *w27, uint32_t *T)
 {
     uint32_t w[3][3][3];
     for (int i = 0; i < 27; ++i) w[i / 9][(i / 3) % 3][i % 3] = w27[i];
-    return kappa3d(w, S, N);
+    return kappa3d(w, T);
 }
+
+void h_count26(const uint32_t *x, uint32_t *o) { count26(x, o); }
 
 uint32_t h_kappa2d(const uint32_t *w9, uint32_t *F, uint32_t *Q)
 {
@@ -28,6 +30,4 @@ uint32_t h_kappa2d(const uint32_t *w9, uint32_t *F, uint32_t *Q)
     return kappa2d(w, F, Q);
 }
 
-void h_count12(const uint32_t *x, uint32_t *o) { count12(x, o); }
-void h_count14(const uint32_t *x, uint32_t *o) { count14(x, o); }
 }

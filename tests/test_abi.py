@@ -50,6 +50,9 @@ def test_null_handles_are_rejected(lib):
     assert lib.ecc_compute(None, None, None, None, None) == ecc.ECC_E_INVALID
     assert lib.ecc_compute_batch(None, 1, None, None, None) == ecc.ECC_E_INVALID
     assert lib.ecc_plan_destroy(None) == ecc.ECC_E_INVALID
+    gave = (ctypes.c_int32 * 2)()
+    assert lib.ecc_selftest_wait_timeout(0, gave, None) == ecc.ECC_E_INVALID
+    assert lib.ecc_selftest_wait_timeout(1000, None, None) == ecc.ECC_E_INVALID
 
 
 def test_python_image_descriptor_from_numpy():

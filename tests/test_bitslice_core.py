@@ -19,12 +19,12 @@ def h(tmp_path_factory):
                     str(ROOT / "tests" / "bitslice_harness.cpp"), "-o", str(out)], check=True)
     lib = ctypes.CDLL(str(out))
     u32p = ctypes.POINTER(ctypes.c_uint32)
-    for n in ("h_transpose_u8", "h_transpose_u16", "h_count12", "h_count14"):
+    for n in ("h_transpose_u8", "h_transpose_u16", "h_count26"):
         getattr(lib, n).argtypes = [u32p, u32p]
     for n in ("h_ge8", "h_ge16"):
         getattr(lib, n).argtypes = [u32p, u32p]
         getattr(lib, n).restype = ctypes.c_uint32
-    lib.h_kappa3d.argtypes = [u32p, u32p, u32p]
+    lib.h_kappa3d.argtypes = [u32p, u32p]
     lib.h_kappa3d.restype = ctypes.c_uint32
     lib.h_kappa2d.argtypes = [u32p, u32p, u32p]
     lib.h_kappa2d.restype = ctypes.c_uint32
@@ -80,15 +80,15 @@ def _vals(planes, nbits):
     return [sum(((int(planes[k]) >> x) & 1) << k for k in range(nbits)) for x in range(32)]
 
 
-@pytest.mark.parametrize("n,fn", [(12, "h_count12"), (14, "h_count14")])
+@pytest.mark.parametrize("n,fn", [(26, "h_count26")])
 def test_counters(h, n, fn):
     rng = np.random.default_rng(3)
     for _ in range(300):
         x = rng.integers(0, 1 << 32, size=n, dtype=np.uint64).astype(np.uint32)
-        o = np.zeros(4, np.uint32)
+        o = np.zeros(5, np.uint32)
         getattr(h, fn)(_p(x), _p(o))
         want = [sum((int(x[i]) >> b) & 1 for i in range(n)) for b in range(32)]
-        assert _vals(o, 4) == want
+        assert _vals(o, 5) == want
 
 
 def kappa3d_scalar(w):
@@ -114,14 +114,13 @@ def test_kappa3d(h):
         for _ in range(40):
             bits = (rng.uniform(size=(27, 32)) < density).astype(np.uint64)
             w27 = np.array([sum(int(bits[i, x]) << x for x in range(32)) for i in range(27)], np.uint32)
-            S = np.zeros(4, np.uint32)
-            N = np.zeros(4, np.uint32)
-            nz = h.h_kappa3d(_p(w27), _p(S), _p(N))
-            s, n = _vals(S, 4), _vals(N, 4)
+            T = np.zeros(5, np.uint32)
+            nz = h.h_kappa3d(_p(w27), _p(T))
+            t = _vals(T, 5)
             for x in range(32):
                 w = bits[:, x].reshape(3, 3, 3).astype(int)
                 kap = kappa3d_scalar(w)
-                assert 1 + s[x] - n[x] == kap
+                assert t[x] - 13 == kap
                 assert ((nz >> x) & 1) == (kap != 0)
 
 
