@@ -63,11 +63,15 @@ def _traffic_for(kernel_digest: str):
     return ent.get("dram_bytes_per_launch")
 
 
+STENCIL_SOURCES = ("ecc_bitslice.cu", "ecc_bitslice.cuh", "ecc_walk.cuh", "ecc_sync.cuh", "ecc_internal.h")
+
+
 def _kernel_digest():
+    """Digest of the sources the 3D stencil kernel is compiled from."""
     import hashlib
     h = hashlib.sha256()
-    for p in sorted((ROOT / "paper_2203_09087_gb300" / "csrc").glob("*")):
-        h.update(p.read_bytes())
+    for name in STENCIL_SOURCES:
+        h.update((ROOT / "paper_2203_09087_gb300" / "csrc" / name).read_bytes())
     return h.hexdigest()[:16]
 
 
@@ -244,6 +248,49 @@ def run_batched(args):
         res[name] = {"ms": ms, "gvox_s": total / ms / 1e6, "launches": ecc.ecc_plan_last_launches(plan)}
     res["speedup"] = res["per_image"]["ms"] / res["batched"]["ms"]
     return res
+
+
+def run_single_u16(args):
+    """The 16-bit single-volume workload: 1024^3 uint16 smoothed field (sigma
+    8) plus 2000 bright blobs, 65536 bins (global int64 bins: the histogram
+    does not fit in shared memory).  Stencil kernel time from CUDA events on
+    the launching stream, L2 flushed before every step; roofline bytes =
+    2 bytes per voxel + 65536 x 8."""
+    import torch
+
+    import paper_2203_09087_gb300 as ecc
+    import synth
+    vol = synth.config3_smooth_blobs_u16(device="cuda")
+    nvox = vol.numel()
+    plan = ecc.ecc_plan("u16", 0, 65535, max_voxels=nvox, flags=ecc.ECC_FLAG_TIME_KERNELS)
+    out = torch.empty(65536, dtype=torch.int64, device="cuda")
+    l2 = torch.cuda.get_device_properties(torch.cuda.current_device()).L2_cache_size
+    flush = torch.empty(2 * l2 + (1 << 20), dtype=torch.uint8, device="cuda")
+    ecc.ecc_compute(plan, vol, out)
+    ecc.ecc_status_get(plan)
+    assert int(out[-1].item()) == 1
+    for _ in range(3):
+        flush.fill_(1)
+        ecc.ecc_compute(plan, vol, out)
+    ecc.ecc_plan_kernel_time(plan)
+    steps = 10
+    st = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    en = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    for i in range(steps):
+        flush.fill_(i & 0xFF)
+        st[i].record()
+        ecc.ecc_compute(plan, vol, out)
+        en[i].record()
+    torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in zip(st, en)) / steps
+    kern_ms, kern_n = ecc.ecc_plan_kernel_time(plan)
+    kern_s = kern_ms / max(kern_n, 1) * 1e-3
+    peak, src = _peaks()
+    alg = nvox * 2 + 65536 * 8
+    return {"workload": "1024^3 uint16, sigma 8 smoothed field + 2000 blobs (seed 2), 65536 bins",
+            "gvox_s": nvox / (ms * 1e-3) / 1e9, "ms_per_step": ms, "kernel_us": kern_s * 1e6,
+            "roofline": {"bound": "hbm", "achieved": alg / kern_s / 1e9, "peak": peak, "unit": "GB/s",
+                         "frac": alg / kern_s / 1e9 / peak, "peak_source": src}}
 
 
 def run_serving(args):
@@ -437,6 +484,7 @@ def main():
         line["cpu_baseline"] = cpu_oracle_sample(vol.cpu().numpy())
     if args.extras and rank == 0:
         line["batched"] = run_batched(args)
+        line["single_u16"] = run_single_u16(args)
         line["serving"] = run_serving(args)
     if rank == 0:
         print(json.dumps(line))

@@ -154,6 +154,32 @@ struct Emitter {
         else
             atomicAdd(acc + bin, (unsigned long long)(long long)kap);
     }
+    // Voxels of mask m with count T - 13 (negated for top cells); element i
+    // of `vals` is the value of window bit i.  Nonzero counts are sparse in
+    // smooth data and almost all +-1, so those take a short loop and only
+    // the rest read their five bit planes.
+    __device__ __forceinline__ void add_sparse3d(uint32_t m, const uint32_t *Tc, const unsigned char *vals) const
+    {
+        const uint32_t c = Tc[2] & Tc[3] & ~Tc[4] & ~Tc[0];
+        const uint32_t p1 = m & c & Tc[1];
+        uint32_t pm = p1 | (m & c & ~Tc[1]);
+        uint32_t other = m & ~pm;
+        auto val = [&](int i) {
+            return K == 8 ? (int)__ldg(vals + i) : (int)__ldg(reinterpret_cast<const unsigned short *>(vals) + i);
+        };
+        while (pm) {
+            const int i = __ffs(pm) - 1;
+            pm &= pm - 1;
+            const int k = ((p1 >> i) & 1u) ? 1 : -1;
+            add(val(i), TOP ? -k : k);
+        }
+        while (other) {
+            const int i = __ffs(other) - 1;
+            other &= other - 1;
+            const int k = bs::bits_at<5>(Tc, i) - 13;
+            add(val(i), TOP ? -k : k);
+        }
+    }
 };
 
 template <int K, bool TOP, int ND>
@@ -219,44 +245,26 @@ __device__ void run_tile(const BatchArgs &a, const BatchImage &im, long long loc
             }
             return walk::load_row_words<NWORDS>(im.data + z * im.pitch_z + y * im.pitch_y, row_bytes, first, w);
         };
-        const int64_t y0 = yt * kOut3 - 1;
-        const bool inner_xy = xw >= 0 && xw + 32 <= im.nx && y0 >= 0 && y0 + 31 < im.ny;
         walk::Walk3d<K, TOP> wk;
         wk.begin(xex, y - 1 >= 0 && y - 1 < im.ny, y + 1 >= 0 && y + 1 < im.ny);
-        auto emit = [&](uint32_t m, const uint32_t *Tc, const uint32_t *A) {
-            walk::emit_aggregated(
-                m, [&](int i) { return bs::bits_at<K>(A, i); },
-                [&](int i) { return TOP ? 13 - bs::bits_at<5>(Tc, i) : bs::bits_at<5>(Tc, i) - 13; }, em.hist, em.acc,
-                em.lo, em.nbins, em.range_check, em.status);
-        };
+        // values of the plane being emitted: this lane's window in global
+        // memory (just read, so cached); see em.add_sparse
+        const unsigned char *vals = im.data;
+        auto emit = [&](uint32_t m, const uint32_t *Tc, const uint32_t *) { em.add_sparse3d(m, Tc, vals); };
         uint32_t wn[NWORDS + 1];
         walk::Rows3<K> r0, r1;
         int sh = fetch(zb - 1, wn);
         walk::planes_from_words<K>(wn, sh, r0.P);
         walk::complete_rows<K>(r0);
         sh = fetch(zb, wn);
-        int64_t z1 = zb;
-        auto load_next = [&](walk::Rows3<K> &r) {   // plane z1 from the prefetched words
-            walk::planes_from_words<K>(wn, sh, r.P);
+        for (int64_t z1 = zb;; ++z1) {
+            walk::planes_from_words<K>(wn, sh, r1.P);
             if (z1 + 1 <= ze) sh = fetch(z1 + 1, wn);
-            walk::complete_rows<K>(r);
-        };
-        auto advance = [&](const walk::Rows3<K> &cur, const walk::Rows3<K> &nxt) {
-            const bool zp = z1 < im.nz, zok = z1 - 1 >= 0;
-            const bool emit_z = z1 - 1 >= zb;
-            if (inner_xy && zp && zok)
-                wk.template step<false>(cur, nxt, zp, zok, emit_z, out_x, emit);
-            else
-                wk.template step<true>(cur, nxt, zp, zok, emit_z, out_x, emit);
-            ++z1;
-        };
-        for (;;) {
-            load_next(r1);
-            advance(r0, r1);
-            if (z1 > ze) break;
-            load_next(r0);
-            advance(r1, r0);
-            if (z1 > ze) break;
+            walk::complete_rows<K>(r1);
+            vals = im.data + (z1 - 1) * im.pitch_z + (row_ok ? y : 0) * im.pitch_y + xw * (K / 8);
+            wk.step(r0, r1, z1 < im.nz, z1 - 1 >= 0, z1 - 1 >= zb, out_x, emit);
+            r0 = r1;
+            if (z1 >= ze) break;
         }
     }
 }

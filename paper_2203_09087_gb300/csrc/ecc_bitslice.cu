@@ -241,11 +241,12 @@ __global__ void __launch_bounds__((NW + 1) * 32, bs3d_min_blocks<T, NW>())
     } else {
         // ------------------------------------------------------ compute warps
         int *my_hist = hist + (warp % HREP) * a.h.nbins;
-        int64_t g = 0;
+        int g = 0, g_slot = 0;  // planes consumed; ring slot and phase of plane g
+        uint32_t g_phase = 0;
         bool ok = true;
         auto wait_full = [&]() -> int {
-            const int s = (int)(g % S);
-            if (!mbar_wait(&full[s], (uint32_t)((g / S) & 1))) {
+            // warp-uniform outcome: the phase completed if any lane saw it
+            if (!__any_sync(0xffffffffu, mbar_wait(&full[g_slot], g_phase))) {
                 if (lane == 0) {
                     atomicOr(a.status, DEV_TIMEOUT);
                     atomicExch(&s_abort, 1);
@@ -253,19 +254,30 @@ __global__ void __launch_bounds__((NW + 1) * 32, bs3d_min_blocks<T, NW>())
                 ok = false;
                 return -1;
             }
-            return s;
+            return g_slot;
+        };
+        auto next_plane = [&]() {
+            ++g;
+            if (++g_slot == S) {
+                g_slot = 0;
+                g_phase ^= 1u;
+            }
         };
         int off = 0;
-        auto fetch = [&](walk::Rows3<K> &r) {
-            // copy this lane's window of step g's stage, release the stage
+        // Copy this lane's window of plane g out of its stage.  The stage is
+        // released after the plane's emission, which reads voxel values there.
+        auto fetch = [&](walk::Rows3<K> &r) -> int {
             const int s = ok ? wait_full() : -1;
+            if (s >= 0) load_window<T>(stages + (size_t)s * STAGE + lane * BWB, off, r.P);
+            next_plane();
+            walk::complete_rows<K>(r);
+            return s;
+        };
+        auto release = [&](int s) {
             if (s >= 0) {
-                load_window<T>(stages + (size_t)s * STAGE + lane * BWB, off, r.P);
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&empty[s]);
             }
-            ++g;
-            walk::complete_rows<K>(r);
         };
         while (ok) {
             // the stage of the next item's first plane says which item it is
@@ -273,7 +285,7 @@ __global__ void __launch_bounds__((NW + 1) * 32, bs3d_min_blocks<T, NW>())
             if (s0 < 0) break;
             const int item = s_item[s0];
             if (item < 0) {
-                ++g;
+                next_plane();
                 break;
             }
             int xt, yt;
@@ -287,39 +299,61 @@ __global__ void __launch_bounds__((NW + 1) * 32, bs3d_min_blocks<T, NW>())
             const uint32_t xex = walk::x_exist_mask(xw, a.nx);
             const bool lane_out = lane >= 1 && lane <= kOut && y < a.ny;
             const uint32_t out_x = lane_out ? (xex & 0x7ffffffeu) : 0u;
-            // interior: every voxel of the window and of the 30 output rows has
-            // all its x and y neighbours
-            const bool inner_xy = xw >= 0 && xw + 32 <= a.nx && y0 >= 0 && y0 + 31 < a.ny;
+            // plane indices fit in int: TMA coordinates are 32-bit
+            const int nz = (int)a.nz, z_first = (int)zb, z_last = (int)ze;
             walk::Walk3d<K, TOP> wk;
             wk.begin(xex, y - 1 >= 0 && y - 1 < a.ny, y + 1 >= 0 && y + 1 < a.ny);
-            auto emit = [&](uint32_t m, const uint32_t *Tc, const uint32_t *A) {
-                walk::emit_aggregated(
-                    m, [&](int i) { return bs::bits_at<K>(A, i); },
-                    [&](int i) { return TOP ? 13 - bs::bits_at<5>(Tc, i) : bs::bits_at<5>(Tc, i) - 13; },
-                    a.smem_hist ? my_hist : nullptr, a.h.acc, a.h.lo, a.h.nbins, a.range_check, a.status);
+            // The plane being emitted: this lane's window in its stage (bit i
+            // of the window is element i).  Nonzero counts are rare in smooth
+            // fields and almost all are +-1 (T = 14 or 12), so those take a
+            // short loop of plain shared-memory atomics; any other count
+            // reads its five bit planes.
+            const unsigned char *vals = stages;
+            auto emit = [&](uint32_t m, const uint32_t *Tc, const uint32_t *) {
+                const uint32_t c = Tc[2] & Tc[3] & ~Tc[4] & ~Tc[0];
+                const uint32_t p1 = m & c & Tc[1];  // T = 14
+                uint32_t pm = p1 | (m & c & ~Tc[1]);  // T = 14 or 12
+                uint32_t other = m & ~pm;
+                auto add = [&](int i, int k) {
+                    const int v = ES == 1 ? (int)vals[i] : (int)reinterpret_cast<const unsigned short *>(vals)[i];
+                    const int bin = v - a.h.lo;
+                    if (a.range_check && (unsigned)bin >= (unsigned)a.h.nbins) {
+                        atomicOr(a.status, DEV_RANGE);
+                        return;
+                    }
+                    if (TOP) k = -k;  // (-1)^d with d = 3 for top cells
+                    if (a.smem_hist)
+                        atomicAdd(&my_hist[bin], k);
+                    else
+                        atomicAdd(a.h.acc + bin, (unsigned long long)(long long)k);
+                };
+                while (pm) {
+                    const int i = __ffs(pm) - 1;
+                    pm &= pm - 1;
+                    add(i, ((p1 >> i) & 1u) ? 1 : -1);
+                }
+                while (other) {
+                    const int i = __ffs(other) - 1;
+                    other &= other - 1;
+                    add(i, bs::bits_at<5>(Tc, i) - 13);
+                }
             };
+            // one walk step per plane; r0 holds plane z1-1, r1 plane z1
             walk::Rows3<K> r0, r1;
-            fetch(r0);  // plane zb-1 (its full barrier already passed)
-            int64_t z1 = zb;
-            auto advance = [&](const walk::Rows3<K> &cur, const walk::Rows3<K> &nxt) {
-                const bool zp = z1 < a.nz, zok = z1 - 1 >= 0;
-                const bool emit_z = z1 - 1 >= zb;
-                if (inner_xy && zp && zok)
-                    wk.template step<false>(cur, nxt, zp, zok, emit_z, out_x, emit);
-                else
-                    wk.template step<true>(cur, nxt, zp, zok, emit_z, out_x, emit);
-                ++z1;
-            };
-            while (ok) {
-                fetch(r1);
-                advance(r0, r1);
-                if (z1 > ze || !ok) break;
-                fetch(r0);
-                advance(r1, r0);
-                if (z1 > ze) break;
+            int s_cur = fetch(r0);  // plane zb-1 (its full barrier already passed)
+            for (int z1 = z_first; ok; ++z1) {
+                const int s_nxt = fetch(r1);
+                if (!ok) break;
+                vals = stages + (size_t)s_cur * STAGE + lane * BWB + off;
+                wk.step(r0, r1, z1 < nz, z1 >= 1, z1 > z_first, out_x, emit);
+                release(s_cur);
+                s_cur = s_nxt;
+                r0 = r1;
+                if (z1 >= z_last) break;
             }
+            release(s_cur);
         }
-        if (lane == 0) s_consumed[warp] = g;
+        if (lane == 0) s_consumed[warp] = (long long)g;
     }
 
     __syncthreads();

@@ -21,36 +21,17 @@ namespace ecc {
 namespace bs {
 
 #if defined(__CUDACC__)
-// Powers of two in constant memory.  A shift written as a multiply by one
-// of them issues on the FMA pipe (x << d = x * 2^d; x >> d = high word of
-// x * 2^(32-d)); because the factor is not a compile-time constant the
-// compiler cannot turn it back into a shift on the integer ALU pipe, which
-// the bit logic of the stencil already saturates.
+// Powers of two in constant memory, for the byte alignment of a window read
+// at an arbitrary offset: (w0 >> s) | (w1 << (32 - s)) as two multiplies by
+// 2^(32-s) (the high and low words), which issue on the FMA pipe instead of
+// the integer pipe that the bit logic keeps busy.  (Plain shifts stay plain:
+// moving all of them to multiplies measured slower.)
 static __constant__ uint32_t kPow2[33] = {
     1u << 0,  1u << 1,  1u << 2,  1u << 3,  1u << 4,  1u << 5,  1u << 6,  1u << 7,  1u << 8,
     1u << 9,  1u << 10, 1u << 11, 1u << 12, 1u << 13, 1u << 14, 1u << 15, 1u << 16, 1u << 17,
     1u << 18, 1u << 19, 1u << 20, 1u << 21, 1u << 22, 1u << 23, 1u << 24, 1u << 25, 1u << 26,
     1u << 27, 1u << 28, 1u << 29, 1u << 30, 1u << 31, 0u};
 #endif
-
-// x << d and x >> d for 0 < d < 32 (multiplies on the FMA pipe on the device)
-BS_HD uint32_t shl_m(uint32_t x, int d)
-{
-#if defined(__CUDA_ARCH__)
-    return x * kPow2[d];
-#else
-    return x << d;
-#endif
-}
-
-BS_HD uint32_t shr_m(uint32_t x, int d)
-{
-#if defined(__CUDA_ARCH__)
-    return __umulhi(x, kPow2[32 - d]);
-#else
-    return x >> d;
-#endif
-}
 
 // Byte permute: result byte i = byte (s >> 4i) & 7 of the 8 bytes {a, b}.
 BS_HD uint32_t byte_perm(uint32_t a, uint32_t b, uint32_t s)
@@ -71,8 +52,8 @@ BS_HD uint32_t byte_perm(uint32_t a, uint32_t b, uint32_t s)
 BS_HD void swap_bit(uint32_t &lo, uint32_t &hi, int d, uint32_t M)
 {
     const uint32_t a = lo, b = hi;
-    lo = (a & ~M) | (shl_m(b, d) & M);
-    hi = (shr_m(a, d) & ~M) | (b & M);
+    lo = (a & ~M) | ((b << d) & M);
+    hi = ((a >> d) & ~M) | (b & M);
 }
 
 // 32 uint8 voxels in r[0..7] (little-endian: byte j of r[q] is voxel 4q+j)

@@ -151,8 +151,9 @@ void ecc_plan_s::autotune()
     if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return;
     const bool range = !(d.flags & ECC_FLAG_NO_RANGE_CHECK);
     if (need3d) {
-        // 3D single-image kernel on a synthetic 352x150x128 volume
-        const int nx = 352, ny = 150, nz = 128;
+        // 3D single-image kernel on a synthetic 512x256x192 volume: large
+        // enough that every tile shape keeps all SMs busy, as in real use
+        const int nx = 512, ny = 256, nz = 192;
         const int64_t n = (int64_t)nx * ny * nz;
         unsigned char *buf = nullptr;
         Choice c;

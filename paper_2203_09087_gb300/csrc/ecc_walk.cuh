@@ -28,9 +28,8 @@ namespace walk {
 __device__ __forceinline__ uint32_t from_next_lane(uint32_t v) { return __shfl_down_sync(0xffffffffu, v, 1); }
 __device__ __forceinline__ uint32_t from_prev_lane(uint32_t v) { return __shfl_up_sync(0xffffffffu, v, 1); }
 
-// One-bit shifts as multiplies on the FMA pipe (see bs::shl_m).
-__device__ __forceinline__ uint32_t shl1(uint32_t x) { return bs::shl_m(x, 1); }
-__device__ __forceinline__ uint32_t shr1(uint32_t x) { return bs::shr_m(x, 1); }
+__device__ __forceinline__ uint32_t shl1(uint32_t x) { return x << 1; }
+__device__ __forceinline__ uint32_t shr1(uint32_t x) { return x >> 1; }
 
 // r[x] = m[x + dx]
 template <int DX>
@@ -156,8 +155,7 @@ __device__ __forceinline__ void emit_aggregated(uint32_t m, ValAt &&val_at, Kapp
 
 // One plane's part of a lane: row y as planes P and row y+1 (the next
 // lane's P) as U.  The one-voxel shifts of P are recomputed where needed
-// (multiplies on the otherwise idle FMA pipe) rather than kept, to save
-// registers.
+// rather than kept, to save registers.
 template <int K>
 struct Rows3 {
     uint32_t P[K], U[K];
@@ -193,12 +191,14 @@ struct Walk3d {
         }
     }
 
-    // From plane z (rows a) to plane z+1 (rows b).  EDGE: apply the existence
-    // masks (zp: plane z+1 exists, z_ok: plane z exists); without EDGE every
-    // neighbour exists (interior tile).  When `emit_z` (warp-uniform), calls
+    // From plane z (rows a) to plane z+1 (rows b); zp: plane z+1 exists,
+    // z_ok: plane z exists.  The existence masks are always applied: one
+    // copy of the step (no interior specialisation) keeps the walk loop
+    // small enough for the instruction cache, which measured faster than
+    // saving the masking logic.  When `emit_z` (warp-uniform), calls
     // emit(mask, T, a.P) for plane z: output voxels with a nonzero count,
     // count = T - 13 before the top-cell sign.  Warp-collective.
-    template <bool EDGE, class Emit>
+    template <class Emit>
     __device__ __forceinline__ void step(const Rows3<K> &a, const Rows3<K> &b, bool zp, bool z_ok, bool emit_z,
                                          uint32_t out_x, Emit &&emit)
     {
@@ -234,10 +234,10 @@ struct Walk3d {
             K2_dn[d] = from_prev_lane(K2[d]);
             F_dn[d] = from_prev_lane(F[d]);
         }
-        const uint32_t ez_p = (!EDGE || zp) ? 0xffffffffu : 0u;
-        const uint32_t ez_m1 = (!EDGE || z_ok) ? 0xffffffffu : 0u;
-        auto ex = [&](int i) { return EDGE ? ex_x[i] : 0xffffffffu; };
-        auto eyy = [&](int i) { return EDGE ? ey[i] : 0xffffffffu; };
+        const uint32_t ez_p = zp ? 0xffffffffu : 0u;
+        const uint32_t ez_m1 = z_ok ? 0xffffffffu : 0u;
+        auto ex = [&](int i) { return ex_x[i]; };
+        auto eyy = [&](int i) { return ey[i]; };
         if (emit_z) {
             uint32_t w[3][3][3];
             w[2][1][0] = at_offset<-1>(H0[0]);
@@ -253,7 +253,7 @@ struct Walk3d {
             for (int dy = 0; dy < 3; ++dy)
 #pragma unroll
                 for (int dx = 0; dx < 3; ++dx) {
-                    if (EDGE) w[2][dy][dx] = with_exist<TOP>(w[2][dy][dx], ez_p & ey[dy] & ex_x[dx]);
+                    w[2][dy][dx] = with_exist<TOP>(w[2][dy][dx], ez_p & ey[dy] & ex_x[dx]);
                     w[0][dy][dx] = Wm[dy][dx];
                 }
             w[1][1][0] = wx0;
