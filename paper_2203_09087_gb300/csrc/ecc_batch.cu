@@ -246,7 +246,8 @@ __device__ void run_tile(const BatchArgs &a, const BatchImage &im, long long loc
             return walk::load_row_words<NWORDS>(im.data + z * im.pitch_z + y * im.pitch_y, row_bytes, first, w);
         };
         walk::Walk3d<K, TOP> wk;
-        wk.begin(xex, y - 1 >= 0 && y - 1 < im.ny, y + 1 >= 0 && y + 1 < im.ny);
+        wk.begin();
+        const uint32_t e_row = row_ok ? ~xex : 0xffffffffu;  // existence plane of this lane's window
         // values of the plane being emitted: this lane's window in global
         // memory (just read, so cached); see em.add_sparse
         const unsigned char *vals = im.data;
@@ -255,14 +256,16 @@ __device__ void run_tile(const BatchArgs &a, const BatchImage &im, long long loc
         walk::Rows3<K> r0, r1;
         int sh = fetch(zb - 1, wn);
         walk::planes_from_words<K>(wn, sh, r0.P);
+        r0.P[K] = zb - 1 >= 0 ? e_row : 0xffffffffu;
         walk::complete_rows<K>(r0);
         sh = fetch(zb, wn);
         for (int64_t z1 = zb;; ++z1) {
             walk::planes_from_words<K>(wn, sh, r1.P);
+            r1.P[K] = z1 < im.nz ? e_row : 0xffffffffu;
             if (z1 + 1 <= ze) sh = fetch(z1 + 1, wn);
             walk::complete_rows<K>(r1);
             vals = im.data + (z1 - 1) * im.pitch_z + (row_ok ? y : 0) * im.pitch_y + xw * (K / 8);
-            wk.step(r0, r1, z1 < im.nz, z1 - 1 >= 0, z1 - 1 >= zb, out_x, emit);
+            wk.step(r0, r1, z1 - 1 >= zb, out_x, emit);
             r0 = r1;
             if (z1 >= ze) break;
         }

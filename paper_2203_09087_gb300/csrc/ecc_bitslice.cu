@@ -266,9 +266,13 @@ __global__ void __launch_bounds__((NW + 1) * 32, bs3d_min_blocks<T, NW>())
         int off = 0;
         // Copy this lane's window of plane g out of its stage.  The stage is
         // released after the plane's emission, which reads voxel values there.
-        auto fetch = [&](walk::Rows3<K> &r) -> int {
+        // e_row: the existence plane of this lane's window in a plane that
+        // exists (set per item); a plane outside the image is all missing.
+        uint32_t e_row = 0;
+        auto fetch = [&](walk::Rows3<K> &r, bool plane_exists) -> int {
             const int s = ok ? wait_full() : -1;
             if (s >= 0) load_window<T>(stages + (size_t)s * STAGE + lane * BWB, off, r.P);
+            r.P[K] = plane_exists ? e_row : 0xffffffffu;
             next_plane();
             walk::complete_rows<K>(r);
             return s;
@@ -299,10 +303,11 @@ __global__ void __launch_bounds__((NW + 1) * 32, bs3d_min_blocks<T, NW>())
             const uint32_t xex = walk::x_exist_mask(xw, a.nx);
             const bool lane_out = lane >= 1 && lane <= kOut && y < a.ny;
             const uint32_t out_x = lane_out ? (xex & 0x7ffffffeu) : 0u;
+            e_row = (y >= 0 && y < a.ny) ? ~xex : 0xffffffffu;
             // plane indices fit in int: TMA coordinates are 32-bit
             const int nz = (int)a.nz, z_first = (int)zb, z_last = (int)ze;
             walk::Walk3d<K, TOP> wk;
-            wk.begin(xex, y - 1 >= 0 && y - 1 < a.ny, y + 1 >= 0 && y + 1 < a.ny);
+            wk.begin();
             // The plane being emitted: this lane's window in its stage (bit i
             // of the window is element i).  Nonzero counts are rare in smooth
             // fields and almost all are +-1 (T = 14 or 12), so those take a
@@ -340,12 +345,12 @@ __global__ void __launch_bounds__((NW + 1) * 32, bs3d_min_blocks<T, NW>())
             };
             // one walk step per plane; r0 holds plane z1-1, r1 plane z1
             walk::Rows3<K> r0, r1;
-            int s_cur = fetch(r0);  // plane zb-1 (its full barrier already passed)
+            int s_cur = fetch(r0, z_first >= 1);  // plane zb-1 (its full barrier already passed)
             for (int z1 = z_first; ok; ++z1) {
-                const int s_nxt = fetch(r1);
+                const int s_nxt = fetch(r1, z1 < nz);
                 if (!ok) break;
                 vals = stages + (size_t)s_cur * STAGE + lane * BWB + off;
-                wk.step(r0, r1, z1 < nz, z1 >= 1, z1 > z_first, out_x, emit);
+                wk.step(r0, r1, z1 > z_first, out_x, emit);
                 release(s_cur);
                 s_cur = s_nxt;
                 r0 = r1;

@@ -154,35 +154,34 @@ __device__ __forceinline__ void emit_aggregated(uint32_t m, ValAt &&val_at, Kapp
 // ------------------------------------------------------------------ 3D
 
 // One plane's part of a lane: row y as planes P and row y+1 (the next
-// lane's P) as U.  The one-voxel shifts of P are recomputed where needed
-// rather than kept, to save registers.
+// lane's P) as U.  Planes 0..K-1 hold the value; plane K is 1 where the
+// voxel does not exist (outside the image), which makes a missing voxel
+// compare above every real one, the value 2^K.  That is exactly the
+// existence rule of both complexes with no masking: in the vertex complex
+// a voxel never beats a missing neighbour (the cell does not exist); in the
+// top-cell complex, where the min wins, it always does (the +infinity
+// collar).  The one-voxel shifts of P are recomputed where needed rather
+// than kept, to save registers.
 template <int K>
 struct Rows3 {
-    uint32_t P[K], U[K];
+    uint32_t P[K + 1], U[K + 1];
 };
 
-// Fill U of a freshly loaded P.  Warp-collective.
+// Fill U of a freshly loaded P (all K + 1 planes).  Warp-collective.
 template <int K>
 __device__ __forceinline__ void complete_rows(Rows3<K> &r)
 {
 #pragma unroll
-    for (int k = 0; k < K; ++k) r.U[k] = from_next_lane(r.P[k]);
+    for (int k = 0; k <= K; ++k) r.U[k] = from_next_lane(r.P[k]);
 }
 
 template <int K, bool TOP>
 struct Walk3d {
+    static constexpr int KP = K + 1;               // value planes + existence plane
     uint32_t wx0, wx2, wyp[3], wym[3], Wm[3][3];   // wins of (z, y) known so far
-    uint32_t ex_x[3], ey[3];                       // neighbour existence along x and y
 
-    // xex: existence of the window's voxels; ym/yp: rows y-1 / y+1 exist.
-    __device__ __forceinline__ void begin(uint32_t xex, bool ym, bool yp)
+    __device__ __forceinline__ void begin()
     {
-        ex_x[0] = xex << 1;
-        ex_x[1] = 0xffffffffu;
-        ex_x[2] = xex >> 1;
-        ey[0] = ym ? 0xffffffffu : 0u;
-        ey[1] = 0xffffffffu;
-        ey[2] = yp ? 0xffffffffu : 0u;
         wx0 = wx2 = 0;
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
@@ -191,41 +190,38 @@ struct Walk3d {
         }
     }
 
-    // From plane z (rows a) to plane z+1 (rows b); zp: plane z+1 exists,
-    // z_ok: plane z exists.  The existence masks are always applied: one
-    // copy of the step (no interior specialisation) keeps the walk loop
-    // small enough for the instruction cache, which measured faster than
-    // saving the masking logic.  When `emit_z` (warp-uniform), calls
-    // emit(mask, T, a.P) for plane z: output voxels with a nonzero count,
-    // count = T - 13 before the top-cell sign.  Warp-collective.
+    // From plane z (rows a) to plane z+1 (rows b).  When `emit_z`
+    // (warp-uniform), calls emit(mask, T, a.P) for plane z: output voxels
+    // with a nonzero count, count = T - 13 before the top-cell sign.
+    // Warp-collective.
     template <class Emit>
-    __device__ __forceinline__ void step(const Rows3<K> &a, const Rows3<K> &b, bool zp, bool z_ok, bool emit_z,
-                                         uint32_t out_x, Emit &&emit)
+    __device__ __forceinline__ void step(const Rows3<K> &a, const Rows3<K> &b, bool emit_z, uint32_t out_x,
+                                         Emit &&emit)
     {
         // plane z against plane z+1 (z earlier): H0[d][x] = A[x-d] vs B[x],
         // Hp[d][x] = A[x-d] vs Bu[x], K2[d][x] = Au[x] vs B[x+d]
         uint32_t H0[3], Hp[3], K2[3], E, F[3];
         {
-            uint32_t Ap[K], Am[K];
-            shifted<K>(a.P, Ap, Am);
-            H0[0] = beats_later<K, TOP>(Ap, b.P);
-            H0[1] = beats_later<K, TOP>(a.P, b.P);
-            H0[2] = beats_later<K, TOP>(Am, b.P);
-            Hp[0] = beats_later<K, TOP>(Ap, b.U);
-            Hp[1] = beats_later<K, TOP>(a.P, b.U);
-            Hp[2] = beats_later<K, TOP>(Am, b.U);
+            uint32_t Ap[KP], Am[KP];
+            shifted<KP>(a.P, Ap, Am);
+            H0[0] = beats_later<KP, TOP>(Ap, b.P);
+            H0[1] = beats_later<KP, TOP>(a.P, b.P);
+            H0[2] = beats_later<KP, TOP>(Am, b.P);
+            Hp[0] = beats_later<KP, TOP>(Ap, b.U);
+            Hp[1] = beats_later<KP, TOP>(a.P, b.U);
+            Hp[2] = beats_later<KP, TOP>(Am, b.U);
         }
         {
-            uint32_t Bp[K], Bm[K];
-            shifted<K>(b.P, Bp, Bm);
-            K2[0] = beats_later<K, TOP>(a.U, Bm);
-            K2[1] = beats_later<K, TOP>(a.U, b.P);
-            K2[2] = beats_later<K, TOP>(a.U, Bp);
+            uint32_t Bp[KP], Bm[KP];
+            shifted<KP>(b.P, Bp, Bm);
+            K2[0] = beats_later<KP, TOP>(a.U, Bm);
+            K2[1] = beats_later<KP, TOP>(a.U, b.P);
+            K2[2] = beats_later<KP, TOP>(a.U, Bp);
             // in-plane pairs of plane z+1: E[x] = B[x-1] vs B[x], F[d][x] = B[x-d] vs Bu[x]
-            E = beats_later<K, TOP>(Bm, b.P);
-            F[0] = beats_later<K, TOP>(Bp, b.U);
-            F[1] = beats_later<K, TOP>(b.P, b.U);
-            F[2] = beats_later<K, TOP>(Bm, b.U);
+            E = beats_later<KP, TOP>(Bm, b.P);
+            F[0] = beats_later<KP, TOP>(Bp, b.U);
+            F[1] = beats_later<KP, TOP>(b.P, b.U);
+            F[2] = beats_later<KP, TOP>(Bm, b.U);
         }
         uint32_t Hp_dn[3], K2_dn[3], F_dn[3];
 #pragma unroll
@@ -234,10 +230,6 @@ struct Walk3d {
             K2_dn[d] = from_prev_lane(K2[d]);
             F_dn[d] = from_prev_lane(F[d]);
         }
-        const uint32_t ez_p = zp ? 0xffffffffu : 0u;
-        const uint32_t ez_m1 = z_ok ? 0xffffffffu : 0u;
-        auto ex = [&](int i) { return ex_x[i]; };
-        auto eyy = [&](int i) { return ey[i]; };
         if (emit_z) {
             uint32_t w[3][3][3];
             w[2][1][0] = at_offset<-1>(H0[0]);
@@ -252,10 +244,7 @@ struct Walk3d {
 #pragma unroll
             for (int dy = 0; dy < 3; ++dy)
 #pragma unroll
-                for (int dx = 0; dx < 3; ++dx) {
-                    w[2][dy][dx] = with_exist<TOP>(w[2][dy][dx], ez_p & ey[dy] & ex_x[dx]);
-                    w[0][dy][dx] = Wm[dy][dx];
-                }
+                for (int dx = 0; dx < 3; ++dx) w[0][dy][dx] = Wm[dy][dx];
             w[1][1][0] = wx0;
             w[1][1][1] = 0;
             w[1][1][2] = wx2;
@@ -269,24 +258,24 @@ struct Walk3d {
             emit(m, T, a.P);
         }
         // wins of (z+1, y) over plane z (an earlier neighbour wins ties)
-        Wm[1][0] = with_exist<TOP>(~H0[2], ez_m1 & eyy(1) & ex(0));
-        Wm[1][1] = with_exist<TOP>(~H0[1], ez_m1 & eyy(1));
-        Wm[1][2] = with_exist<TOP>(~H0[0], ez_m1 & eyy(1) & ex(2));
-        Wm[2][0] = with_exist<TOP>(~at_offset<-1>(K2[2]), ez_m1 & eyy(2) & ex(0));
-        Wm[2][1] = with_exist<TOP>(~K2[1], ez_m1 & eyy(2));
-        Wm[2][2] = with_exist<TOP>(~at_offset<+1>(K2[0]), ez_m1 & eyy(2) & ex(2));
-        Wm[0][0] = with_exist<TOP>(~Hp_dn[2], ez_m1 & eyy(0) & ex(0));
-        Wm[0][1] = with_exist<TOP>(~Hp_dn[1], ez_m1 & eyy(0));
-        Wm[0][2] = with_exist<TOP>(~Hp_dn[0], ez_m1 & eyy(0) & ex(2));
+        Wm[1][0] = ~H0[2];
+        Wm[1][1] = ~H0[1];
+        Wm[1][2] = ~H0[0];
+        Wm[2][0] = ~at_offset<-1>(K2[2]);
+        Wm[2][1] = ~K2[1];
+        Wm[2][2] = ~at_offset<+1>(K2[0]);
+        Wm[0][0] = ~Hp_dn[2];
+        Wm[0][1] = ~Hp_dn[1];
+        Wm[0][2] = ~Hp_dn[0];
         // in-plane wins of (z+1, y)
-        wx2 = with_exist<TOP>(at_offset<+1>(E), ex(2));
-        wx0 = with_exist<TOP>(~E, ex(0));
-        wyp[0] = with_exist<TOP>(at_offset<-1>(F[0]), eyy(2) & ex(0));
-        wyp[1] = with_exist<TOP>(F[1], eyy(2));
-        wyp[2] = with_exist<TOP>(at_offset<+1>(F[2]), eyy(2) & ex(2));
-        wym[0] = with_exist<TOP>(~F_dn[2], eyy(0) & ex(0));
-        wym[1] = with_exist<TOP>(~F_dn[1], eyy(0));
-        wym[2] = with_exist<TOP>(~F_dn[0], eyy(0) & ex(2));
+        wx2 = at_offset<+1>(E);
+        wx0 = ~E;
+        wyp[0] = at_offset<-1>(F[0]);
+        wyp[1] = F[1];
+        wyp[2] = at_offset<+1>(F[2]);
+        wym[0] = ~F_dn[2];
+        wym[1] = ~F_dn[1];
+        wym[2] = ~F_dn[0];
     }
 };
 
