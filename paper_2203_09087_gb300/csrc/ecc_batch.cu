@@ -136,54 +136,8 @@ __global__ void __launch_bounds__(1024) build_worklist(BatchArgs a)
     if (tid == 0) a.start[n] = s_carry;
 }
 
-template <int K, bool TOP>
-struct Emitter {
-    int *hist;                 // this warp's shared bins, or null for global
-    unsigned long long *acc;   // this image's global bins
-    int lo, nbins, range_check;
-    unsigned int *status;
-    __device__ __forceinline__ void add(int v, int kap) const
-    {
-        const int bin = v - lo;
-        if (range_check && (unsigned)bin >= (unsigned)nbins) {
-            atomicOr(status, DEV_RANGE);
-            return;
-        }
-        if (hist)
-            atomicAdd(&hist[bin], kap);
-        else
-            atomicAdd(acc + bin, (unsigned long long)(long long)kap);
-    }
-    // Voxels of mask m with count T - 13 (negated for top cells); element i
-    // of `vals` is the value of window bit i.  Nonzero counts are sparse in
-    // smooth data and almost all +-1, so those take a short loop and only
-    // the rest read their five bit planes.
-    __device__ __forceinline__ void add_sparse3d(uint32_t m, const uint32_t *Tc, const unsigned char *vals) const
-    {
-        const uint32_t c = Tc[2] & Tc[3] & ~Tc[4] & ~Tc[0];
-        const uint32_t p1 = m & c & Tc[1];
-        uint32_t pm = p1 | (m & c & ~Tc[1]);
-        uint32_t other = m & ~pm;
-        auto val = [&](int i) {
-            return K == 8 ? (int)__ldg(vals + i) : (int)__ldg(reinterpret_cast<const unsigned short *>(vals) + i);
-        };
-        while (pm) {
-            const int i = __ffs(pm) - 1;
-            pm &= pm - 1;
-            const int k = ((p1 >> i) & 1u) ? 1 : -1;
-            add(val(i), TOP ? -k : k);
-        }
-        while (other) {
-            const int i = __ffs(other) - 1;
-            other &= other - 1;
-            const int k = bs::bits_at<5>(Tc, i) - 13;
-            add(val(i), TOP ? -k : k);
-        }
-    }
-};
-
 template <int K, bool TOP, int ND>
-__device__ void run_tile(const BatchArgs &a, const BatchImage &im, long long local, const Emitter<K, TOP> &em,
+__device__ void run_tile(const BatchArgs &a, const BatchImage &im, long long local, const walk::Bins &em,
                          int lane)
 {
     constexpr int NWORDS = K;
@@ -216,11 +170,16 @@ __device__ void run_tile(const BatchArgs &a, const BatchImage &im, long long loc
             walk::planes_from_words<K>(wn, sh, B);
             if (y1 + 1 <= ye) sh = fetch(y1 + 1, wn);
             wk.step(B, y1 < im.ny, y1 - 1 >= 0, y1 - 1 >= yb, out_x,
-                    [&](uint32_t m, const uint32_t *Q, const uint32_t *F, const uint32_t *A) {
-                        walk::emit_aggregated(
-                            m, [&](int i) { return bs::bits_at<K>(A, i); },
-                            [&](int i) { return 1 + bs::bits_at<3>(Q, i) - bs::bits_at<3>(F, i); }, em.hist, em.acc,
-                            em.lo, em.nbins, em.range_check, em.status);
+                    [&](uint32_t m, const uint32_t *Q, const uint32_t *F, const uint32_t *) {
+                        // values of row y1-1, just read (cached)
+                        const unsigned char *row = im.data + (y1 - 1) * im.pitch_y + xw * (K / 8);
+                        walk::emit_sparse2d(
+                            m, Q, F,
+                            [&](int i) {
+                                return K == 8 ? (int)__ldg(row + i)
+                                              : (int)__ldg(reinterpret_cast<const unsigned short *>(row) + i);
+                            },
+                            em);
                     });
         }
     } else {
@@ -249,9 +208,16 @@ __device__ void run_tile(const BatchArgs &a, const BatchImage &im, long long loc
         wk.begin();
         const uint32_t e_row = row_ok ? ~xex : 0xffffffffu;  // existence plane of this lane's window
         // values of the plane being emitted: this lane's window in global
-        // memory (just read, so cached); see em.add_sparse
+        // memory (just read, so cached)
         const unsigned char *vals = im.data;
-        auto emit = [&](uint32_t m, const uint32_t *Tc, const uint32_t *) { em.add_sparse3d(m, Tc, vals); };
+        auto emit = [&](uint32_t m, const uint32_t *Tc, const uint32_t *) {
+            walk::emit_sparse3d<TOP>(
+                m, Tc,
+                [&](int i) {
+                    return K == 8 ? (int)__ldg(vals + i) : (int)__ldg(reinterpret_cast<const unsigned short *>(vals) + i);
+                },
+                em);
+        };
         uint32_t wn[NWORDS + 1];
         walk::Rows3<K> r0, r1;
         int sh = fetch(zb - 1, wn);
@@ -317,7 +283,7 @@ __global__ void __launch_bounds__(kBatchWarps * 32, 1) batch_kernel(BatchArgs a)
             cur = lo;
         }
         const BatchImage im = a.img[lo];
-        Emitter<K, TOP> em{hist, a.acc + (size_t)lo * a.nbins, a.lo, a.nbins, a.range_check, a.status};
+        const walk::Bins em{hist, a.acc + (size_t)lo * a.nbins, a.lo, a.nbins, a.range_check, a.status};
         if (im.ndim == 2)
             run_tile<K, TOP, 2>(a, im, item - a.start[lo], em, lane);
         else

@@ -309,39 +309,17 @@ __global__ void __launch_bounds__((NW + 1) * 32, bs3d_min_blocks<T, NW>())
             walk::Walk3d<K, TOP> wk;
             wk.begin();
             // The plane being emitted: this lane's window in its stage (bit i
-            // of the window is element i).  Nonzero counts are rare in smooth
-            // fields and almost all are +-1 (T = 14 or 12), so those take a
-            // short loop of plain shared-memory atomics; any other count
-            // reads its five bit planes.
+            // of the window is element i), read only for emitted voxels.
             const unsigned char *vals = stages;
+            const walk::Bins bins{a.smem_hist ? my_hist : nullptr, a.h.acc, a.h.lo, a.h.nbins, a.range_check,
+                                  a.status};
             auto emit = [&](uint32_t m, const uint32_t *Tc, const uint32_t *) {
-                const uint32_t c = Tc[2] & Tc[3] & ~Tc[4] & ~Tc[0];
-                const uint32_t p1 = m & c & Tc[1];  // T = 14
-                uint32_t pm = p1 | (m & c & ~Tc[1]);  // T = 14 or 12
-                uint32_t other = m & ~pm;
-                auto add = [&](int i, int k) {
-                    const int v = ES == 1 ? (int)vals[i] : (int)reinterpret_cast<const unsigned short *>(vals)[i];
-                    const int bin = v - a.h.lo;
-                    if (a.range_check && (unsigned)bin >= (unsigned)a.h.nbins) {
-                        atomicOr(a.status, DEV_RANGE);
-                        return;
-                    }
-                    if (TOP) k = -k;  // (-1)^d with d = 3 for top cells
-                    if (a.smem_hist)
-                        atomicAdd(&my_hist[bin], k);
-                    else
-                        atomicAdd(a.h.acc + bin, (unsigned long long)(long long)k);
-                };
-                while (pm) {
-                    const int i = __ffs(pm) - 1;
-                    pm &= pm - 1;
-                    add(i, ((p1 >> i) & 1u) ? 1 : -1);
-                }
-                while (other) {
-                    const int i = __ffs(other) - 1;
-                    other &= other - 1;
-                    add(i, bs::bits_at<5>(Tc, i) - 13);
-                }
+                walk::emit_sparse3d<TOP>(
+                    m, Tc,
+                    [&](int i) {
+                        return ES == 1 ? (int)vals[i] : (int)reinterpret_cast<const unsigned short *>(vals)[i];
+                    },
+                    bins);
             };
             // one walk step per plane; r0 holds plane z1-1, r1 plane z1
             walk::Rows3<K> r0, r1;
@@ -443,11 +421,18 @@ __global__ void __launch_bounds__(kWarps2d * 32) bs2d_kernel(const Bs2dArgs a)
             }
             return walk::load_row_words<K>(a.data + yy * a.pitch, row_bytes, first, w);
         };
-        auto emit = [&](uint32_t m, const uint32_t *Q, const uint32_t *F, const uint32_t *A) {
-            walk::emit_aggregated(
-                m, [&](int i) { return bs::bits_at<K>(A, i); },
-                [&](int i) { return 1 + bs::bits_at<3>(Q, i) - bs::bits_at<3>(F, i); },  // (-1)^2 = +1
-                a.smem_hist ? my_hist : nullptr, a.h.acc, a.h.lo, a.h.nbins, a.range_check, a.status);
+        // values of emitted voxels come from the row just read (cached)
+        const walk::Bins bins{a.smem_hist ? my_hist : nullptr, a.h.acc, a.h.lo, a.h.nbins, a.range_check,
+                              a.status};
+        int64_t y1 = yb;
+        auto emit = [&](uint32_t m, const uint32_t *Q, const uint32_t *F, const uint32_t *) {
+            const unsigned char *row = a.data + (y1 - 1) * a.pitch + xw * ES;
+            walk::emit_sparse2d(
+                m, Q, F,
+                [&](int i) {
+                    return ES == 1 ? (int)__ldg(row + i) : (int)__ldg(reinterpret_cast<const unsigned short *>(row) + i);
+                },
+                bins);
         };
         uint32_t wn[K + 1], P[K];
         int sh = fetch(yb - 1, wn);
@@ -455,7 +440,7 @@ __global__ void __launch_bounds__(kWarps2d * 32) bs2d_kernel(const Bs2dArgs a)
         walk::Walk2d<K, TOP> wk;
         wk.begin(P, xex);
         sh = fetch(yb, wn);
-        for (int64_t y1 = yb; y1 <= ye; ++y1) {
+        for (; y1 <= ye; ++y1) {
             uint32_t B[K];
             walk::planes_from_words<K>(wn, sh, B);
             if (y1 + 1 <= ye) sh = fetch(y1 + 1, wn);  // prefetch the next row

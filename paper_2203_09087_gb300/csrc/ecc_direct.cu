@@ -48,18 +48,28 @@ __device__ __forceinline__ bool beats(int c, int q, bool later, bool exists)
     return exists && (later ? c >= q : c > q);
 }
 
+// Adds each thread's voxel count to its bin, aggregated per warp: the
+// lanes of a warp are 32 consecutive voxels of a row, which in smooth data
+// often share a gray level, so lanes adding to the same bin in this step
+// are grouped with __match_any_sync and one of them adds the group's sum
+// (__reduce_add_sync).  Called by every thread that walks a voxel (the
+// active threads of a warp are converged here).
 __device__ __forceinline__ void add_bin(const DirectArgs &a, int *s_hist, int value, int kappa)
 {
-    if (kappa == 0) return;
-    const int bin = value - a.h.lo;
-    if (a.range_check && (bin < 0 || bin >= a.h.nbins)) {
+    int bin = kappa ? value - a.h.lo : -1;
+    if (kappa && a.range_check && (unsigned)bin >= (unsigned)a.h.nbins) {
         atomicOr(a.status, DEV_RANGE);
-        return;
+        bin = -1;
     }
+    const unsigned active = __activemask();
+    if (!__any_sync(active, bin >= 0)) return;
+    const unsigned peers = __match_any_sync(active, bin);
+    const int sum = __reduce_add_sync(peers, bin >= 0 ? kappa : 0);
+    if (bin < 0 || sum == 0 || (int)(threadIdx.x & 31) != __ffs(peers) - 1) return;
     if (a.smem_hist)
-        atomicAdd(&s_hist[bin], kappa);
+        atomicAdd(&s_hist[bin], sum);
     else
-        atomicAdd(a.h.acc + bin, (unsigned long long)(long long)kappa);
+        atomicAdd(a.h.acc + bin, (unsigned long long)(long long)sum);
 }
 
 template <typename T, bool TOP>
