@@ -92,6 +92,7 @@ typedef struct ecc_image {
 #define ECC_FLAG_KERNEL_BITSLICE  0x20u /* force the bit-sliced stencil kernel (where it applies) */
 #define ECC_FLAG_BATCH_PER_IMAGE  0x40u /* ecc_compute_batch: one stencil launch per image (baseline) */
 #define ECC_FLAG_TIME_KERNELS     0x80u /* record CUDA events around every stencil launch */
+#define ECC_FLAG_COUNT_EMITTED    0x100u /* single-image stencils count voxels with a nonzero count */
 
 typedef struct ecc_plan_desc {
     int32_t dtype;          /* ecc_dtype of every image computed with this plan */
@@ -193,6 +194,15 @@ int32_t ecc_plan_last_launches(ecc_plan_t plan);
  * how many launches that covers.  Waits for the recorded events; resets the
  * record.  Errors: ECC_E_INVALID (flag not set), ECC_E_CUDA. */
 ecc_status ecc_plan_kernel_time(ecc_plan_t plan, double *ms, int64_t *launches);
+
+/* With ECC_FLAG_COUNT_EMITTED: number of voxels whose signed cell count
+ * kappa (Sec. 2.3, the terms of Algorithm 1 regrouped per voxel) was nonzero
+ * in the ecc_compute / ecc_compute_host calls since the previous call, i.e.
+ * the histogram insertions the stencil made.  Counted by the single-image
+ * stencil kernels only (not by ecc_compute_batch).  Synchronizes `stream`,
+ * then resets the count.  Errors: ECC_E_INVALID (NULL argument, flag not
+ * set), ECC_E_CUDA. */
+ecc_status ecc_plan_emitted(ecc_plan_t plan, int64_t *count, void *stream);
 
 /* Failure-detection self-test: launches one warp that waits on a device flag
  * nothing sets (the scan's look-back pattern) and then on an mbarrier nothing

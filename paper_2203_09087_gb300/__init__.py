@@ -29,6 +29,7 @@ from ._binding import (  # noqa: F401
     ECC_FLAG_NO_AUTOTUNE,
     ECC_FLAG_NO_RANGE_CHECK,
     ECC_FLAG_TIME_KERNELS,
+    ECC_FLAG_COUNT_EMITTED,
     ECC_OK,
     ECC_TOPCELL_MIN,
     ECC_U8,
@@ -45,6 +46,7 @@ from ._binding import (  # noqa: F401
     ecc_plan,
     ecc_plan_destroy,
     ecc_plan_kernel_time,
+    ecc_plan_emitted,
     ecc_plan_last_launches,
     ecc_plan_nbins,
     ecc_selftest_wait_timeout,

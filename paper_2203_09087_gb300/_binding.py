@@ -21,6 +21,7 @@ ECC_FLAG_KERNEL_DIRECT = 0x10
 ECC_FLAG_KERNEL_BITSLICE = 0x20
 ECC_FLAG_BATCH_PER_IMAGE = 0x40
 ECC_FLAG_TIME_KERNELS = 0x80
+ECC_FLAG_COUNT_EMITTED = 0x100
 
 _STATUS_NAMES = {0: "ECC_OK", 1: "ECC_E_INVALID", 2: "ECC_E_RANGE", 3: "ECC_E_NOMEM", 4: "ECC_E_CUDA",
                  5: "ECC_E_TIMEOUT", 6: "ECC_E_BUSY", 7: "ECC_E_SHUTDOWN", 8: "ECC_E_CANCELLED"}
@@ -63,6 +64,7 @@ _SIGNATURES = {
                                            _VP]),
     "ecc_status_get": (ctypes.c_int, [_VP, _VP]),
     "ecc_plan_kernel_time": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_I64)]),
+    "ecc_plan_emitted": (ctypes.c_int, [_VP, ctypes.POINTER(_I64), _VP]),
     "ecc_last_error": (ctypes.c_char_p, []),
     "ecc_selftest_wait_timeout": (ctypes.c_int, [_I64, ctypes.POINTER(ctypes.c_int32), _VP]),
     "ecc_server_create": (ctypes.c_int, [ctypes.POINTER(_VP), ctypes.POINTER(EccServerDesc)]),
@@ -273,6 +275,13 @@ def ecc_plan_kernel_time(plan: Plan):
     n = ctypes.c_int64()
     _check(library().ecc_plan_kernel_time(plan.handle, ctypes.byref(ms), ctypes.byref(n)))
     return ms.value, n.value
+
+
+def ecc_plan_emitted(plan: Plan, stream=None) -> int:
+    """Voxels with a nonzero signed count since the last call (needs ECC_FLAG_COUNT_EMITTED)."""
+    n = ctypes.c_int64()
+    _check(library().ecc_plan_emitted(plan.handle, ctypes.byref(n), _stream_handle(stream)))
+    return n.value
 
 
 def ecc_compute_noalloc(image, lo: int = 0, hi: int | None = None, complex_mode: int = ECC_VERTEX_MAX,

@@ -205,6 +205,20 @@ ecc_status ecc_plan_kernel_time(ecc_plan_t p, double *ms, int64_t *launches)
     return ECC_OK;
 }
 
+ecc_status ecc_plan_emitted(ecc_plan_t p, int64_t *count, void *stream)
+{
+    if (!p || !count) return invalid("ecc_plan_emitted: NULL argument");
+    if (!(p->d.flags & ECC_FLAG_COUNT_EMITTED)) return invalid("ecc_plan_emitted: plan lacks ECC_FLAG_COUNT_EMITTED");
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    unsigned long long v = 0;
+    cudaError_t e = cudaMemcpyAsync(&v, p->emitted, sizeof(v), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p->emitted, 0, sizeof(v), s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "ecc_plan_emitted");
+    *count = (int64_t)v;
+    return ECC_OK;
+}
+
 ecc_status ecc_compute(ecc_plan_t p, const ecc_image *img, int64_t *d_ecc, int64_t *d_vcec, void *stream)
 {
     if (!p) return invalid("ecc_compute: NULL plan");
@@ -215,6 +229,7 @@ ecc_status ecc_compute(ecc_plan_t p, const ecc_image *img, int64_t *d_ecc, int64
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     p->last_launches = 0;
     HistDst h{p->acc, p->d.lo, p->nbins};
+    if (p->d.flags & ECC_FLAG_COUNT_EMITTED) h.emitted = p->emitted;
     const int64_t outer = g.ndim == 3 ? g.nz : g.ny;
     cudaError_t e = launch_stencil(p, g, 0, outer, h, s);
     if (e != cudaSuccess) return cuda_fail(e, "ecc_compute: stencil launch");
@@ -278,6 +293,7 @@ ecc_status ecc_compute_host(ecc_plan_t p, const ecc_image *h_img, int64_t *h_ecc
     p->last_launches = 0;
     cudaError_t e = cudaSuccess;
     HistDst h{p->acc, p->d.lo, p->nbins};
+    if (p->d.flags & ECC_FLAG_COUNT_EMITTED) h.emitted = p->emitted;
     for (int64_t k = 0; k < nchunks && e == cudaSuccess; ++k) {
         const int64_t a = cut[k], b = cut[k + 1];
         unsigned char *dst = p->stage + a * outer_bytes;

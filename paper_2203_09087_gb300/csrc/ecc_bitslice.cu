@@ -241,6 +241,7 @@ __global__ void __launch_bounds__((NW + 1) * 32, bs3d_min_blocks<T, NW>())
     } else {
         // ------------------------------------------------------ compute warps
         int *my_hist = hist + (warp % HREP) * a.h.nbins;
+        unsigned n_emitted = 0;  // ECC_FLAG_COUNT_EMITTED
         int g = 0, g_slot = 0;  // planes consumed; ring slot and phase of plane g
         uint32_t g_phase = 0;
         bool ok = true;
@@ -314,6 +315,7 @@ __global__ void __launch_bounds__((NW + 1) * 32, bs3d_min_blocks<T, NW>())
             const walk::Bins bins{a.smem_hist ? my_hist : nullptr, a.h.acc, a.h.lo, a.h.nbins, a.range_check,
                                   a.status};
             auto emit = [&](uint32_t m, const uint32_t *Tc, const uint32_t *) {
+                if (a.h.emitted) n_emitted += __popc(m);
                 walk::emit_sparse3d<TOP>(
                     m, Tc,
                     [&](int i) {
@@ -337,6 +339,10 @@ __global__ void __launch_bounds__((NW + 1) * 32, bs3d_min_blocks<T, NW>())
             release(s_cur);
         }
         if (lane == 0) s_consumed[warp] = (long long)g;
+        if (a.h.emitted) {
+            const unsigned n = __reduce_add_sync(0xffffffffu, n_emitted);
+            if (lane == 0 && n) atomicAdd(a.h.emitted, (unsigned long long)n);
+        }
     }
 
     __syncthreads();
@@ -391,7 +397,7 @@ struct Bs2dArgs {
 constexpr int kWarps2d = 4;
 
 template <typename T, bool TOP, int HREP>
-__global__ void __launch_bounds__(kWarps2d * 32) bs2d_kernel(const Bs2dArgs a)
+__global__ void __launch_bounds__(kWarps2d * 32, 4) bs2d_kernel(const Bs2dArgs a)
 {
     using C = Cfg<T>;
     constexpr int K = C::K, ES = C::ES;
@@ -426,6 +432,7 @@ __global__ void __launch_bounds__(kWarps2d * 32) bs2d_kernel(const Bs2dArgs a)
                               a.status};
         int64_t y1 = yb;
         auto emit = [&](uint32_t m, const uint32_t *Q, const uint32_t *F, const uint32_t *) {
+            if (a.h.emitted && m) atomicAdd(a.h.emitted, (unsigned long long)__popc(m));  // diagnostic count
             const unsigned char *row = a.data + (y1 - 1) * a.pitch + xw * ES;
             walk::emit_sparse2d(
                 m, Q, F,

@@ -62,6 +62,10 @@ __device__ __forceinline__ void add_bin(const DirectArgs &a, int *s_hist, int va
         bin = -1;
     }
     const unsigned active = __activemask();
+    if (a.h.emitted) {
+        const unsigned nz = __ballot_sync(active, kappa != 0);
+        if (nz && (int)(threadIdx.x & 31) == __ffs(active) - 1) atomicAdd(a.h.emitted, (unsigned long long)__popc(nz));
+    }
     if (!__any_sync(active, bin >= 0)) return;
     const unsigned peers = __match_any_sync(active, bin);
     const int sum = __reduce_add_sync(peers, bin >= 0 ? kappa : 0);

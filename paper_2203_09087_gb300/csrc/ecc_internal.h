@@ -38,6 +38,7 @@ struct HistDst {
     unsigned long long *acc;    // int64 bins, accumulated with atomics
     int32_t lo;
     int32_t nbins;
+    unsigned long long *emitted = nullptr;  // if set: += voxels with a nonzero count
 };
 
 // Decoupled-lookback scan workspace (self-cleaning: the last CTA of every

@@ -35,6 +35,7 @@ ecc_status ecc_plan_s::allocate()
     b += status_bytes;
     scan_counters = reinterpret_cast<unsigned int *>(b);
     sched = scan_counters + 16;  // same 256-byte block, separate words
+    emitted = reinterpret_cast<unsigned long long *>(scan_counters + 32);
     b += counters_bytes;
     tile_status = reinterpret_cast<int *>(b);
     b += tstat_bytes;

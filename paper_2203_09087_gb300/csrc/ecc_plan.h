@@ -30,6 +30,7 @@ struct ecc_plan_s {
     unsigned int *status = nullptr;      // device status word (ecc::DEV_*)
     unsigned int *scan_counters = nullptr;
     unsigned int *sched = nullptr;       // stencil work counter (2 words, self-resetting)
+    unsigned long long *emitted = nullptr;  // ECC_FLAG_COUNT_EMITTED counter
     int *tile_status = nullptr;
     long long *tile_value = nullptr;
     int32_t max_tiles = 0;

@@ -218,3 +218,51 @@ def test_every_3d_tile_variant(tile, monkeypatch):
         hi = 255 if dt == np.uint8 else 65535
         for mode in MODES:
             assert np.array_equal(_run(_gpu(img), 0, hi, mode), _expect(img, 0, hi, mode)), (tile, shape, mode)
+
+
+def _nonzero_kappa_count(img: np.ndarray) -> int:
+    """Voxels whose signed count of introduced cells is nonzero (vertex
+    complex), by brute force over the cells around each voxel: p introduces
+    a cell iff it beats every other vertex, where p beats q iff I[p] > I[q]
+    or I[p] == I[q] and p comes first in memory; cells with a vertex outside
+    the image do not exist (the neighbour is padded with +infinity)."""
+    import itertools
+    d = img.ndim
+    n = img.size
+    lin = np.arange(n, dtype=np.int64).reshape(img.shape)
+    key = img.astype(np.int64) * n + (n - 1 - lin)
+    big = np.iinfo(np.int64).max
+    pad = np.pad(key, 1, constant_values=big)
+    center = tuple(slice(1, 1 + s) for s in img.shape)
+    c = pad[center]
+
+    def beats(off):
+        sl = tuple(slice(1 + o, 1 + o + s) for o, s in zip(off, img.shape))
+        return c > pad[sl]
+
+    kappa = np.ones(img.shape, np.int64)
+    for sgn in itertools.product((-1, 0, 1), repeat=d):
+        if not any(sgn):
+            continue
+        dim = sum(1 for s in sgn if s)
+        verts = [t for t in itertools.product(*[(0, s) if s else (0,) for s in sgn]) if any(t)]
+        m = np.ones(img.shape, bool)
+        for t in verts:
+            m &= beats(t)
+        kappa += (-1) ** dim * m
+    return int(np.count_nonzero(kappa))
+
+
+@pytest.mark.parametrize("kernel", list(KERNELS))
+@pytest.mark.parametrize("shape", [(100, 77), (17, 40, 129), (9, 97, 31)])
+def test_emitted_count_is_the_nonzero_kappa_count(shape, kernel):
+    ecc = ecc_mod()
+    rng = np.random.default_rng(7)
+    img = rng.integers(0, 6, size=shape, dtype=np.uint8)   # plateaus and ties
+    plan = ecc.ecc_plan("u8", 0, 255, max_voxels=img.size, flags=KERNELS[kernel] | ecc.ECC_FLAG_COUNT_EMITTED)
+    out = torch.empty(256, dtype=torch.int64, device="cuda")
+    ecc.ecc_compute(plan, _gpu(img), out)
+    ecc.ecc_status_get(plan)
+    assert ecc.ecc_plan_emitted(plan) == _nonzero_kappa_count(img)
+    assert ecc.ecc_plan_emitted(plan) == 0   # read resets
+    assert np.array_equal(out.cpu().numpy(), _expect(img, 0, 255, "vertex"))
