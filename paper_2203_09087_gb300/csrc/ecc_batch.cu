@@ -170,11 +170,11 @@ __device__ void run_tile(const BatchArgs &a, const BatchImage &im, long long loc
             walk::planes_from_words<K>(wn, sh, B);
             if (y1 + 1 <= ye) sh = fetch(y1 + 1, wn);
             wk.step(B, y1 < im.ny, y1 - 1 >= 0, y1 - 1 >= yb, out_x,
-                    [&](uint32_t m, const uint32_t *Q, const uint32_t *F, const uint32_t *) {
+                    [&](uint32_t m, const uint32_t *X, const uint32_t *) {
                         // values of row y1-1, just read (cached)
                         const unsigned char *row = im.data + (y1 - 1) * im.pitch_y + xw * (K / 8);
                         walk::emit_sparse2d(
-                            m, Q, F,
+                            m, X,
                             [&](int i) {
                                 return K == 8 ? (int)__ldg(row + i)
                                               : (int)__ldg(reinterpret_cast<const unsigned short *>(row) + i);

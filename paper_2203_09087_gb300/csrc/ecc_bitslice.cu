@@ -431,11 +431,11 @@ __global__ void __launch_bounds__(kWarps2d * 32, 4) bs2d_kernel(const Bs2dArgs a
         const walk::Bins bins{a.smem_hist ? my_hist : nullptr, a.h.acc, a.h.lo, a.h.nbins, a.range_check,
                               a.status};
         int64_t y1 = yb;
-        auto emit = [&](uint32_t m, const uint32_t *Q, const uint32_t *F, const uint32_t *) {
+        auto emit = [&](uint32_t m, const uint32_t *X, const uint32_t *) {
             if (a.h.emitted && m) atomicAdd(a.h.emitted, (unsigned long long)__popc(m));  // diagnostic count
             const unsigned char *row = a.data + (y1 - 1) * a.pitch + xw * ES;
             walk::emit_sparse2d(
-                m, Q, F,
+                m, X,
                 [&](int i) {
                     return ES == 1 ? (int)__ldg(row + i) : (int)__ldg(reinterpret_cast<const unsigned short *>(row) + i);
                 },
@@ -595,10 +595,29 @@ cudaError_t launch_t(const Geom &g, int64_t zb, int64_t ze, const HistDst &h, bo
     const int64_t ctas_max = (int64_t)num_sms * per_sm;
     const int64_t cols = (int64_t)a.ntx * a.nty;
     const int64_t depth = ze - zb;
-    // z-chunks: several items per CTA (they are handed out dynamically), each >= 8 planes
-    int64_t nzc = (6 * ctas_max + cols - 1) / cols;
-    if (nzc > (depth + 7) / 8) nzc = (depth + 7) / 8;
-    if (nzc < 1) nzc = 1;
+    // z-chunks.  An item costs its planes plus two (the halo plane and the
+    // step that emits nothing); CTAs take items dynamically, so the launch
+    // costs about (waves of ctas_max items) x (item cost), a partial last
+    // wave costing a whole one.  Candidates fill k waves (k = 1, 2, ...);
+    // a single wave is charged 10 % more, as nothing then hides a CTA's
+    // start-up (ring fill, histogram clear and flush) -- measured.
+    int64_t nzc = 1;
+    {
+        double best = -1.0;
+        for (int64_t k = 1; k <= 64; ++k) {
+            int64_t n = k * ctas_max / cols;
+            if (n < 1) n = 1;
+            const int64_t zc = (depth + n - 1) / n;
+            n = (depth + zc - 1) / zc;
+            if (zc < 8 && k > 1) break;
+            const int64_t waves = (cols * n + ctas_max - 1) / ctas_max;
+            const double cost = (double)waves * (double)(zc + 2) * (waves == 1 ? 1.1 : 1.0);
+            if (best < 0.0 || cost < best) {
+                best = cost;
+                nzc = n;
+            }
+        }
+    }
     a.zchunk = (int32_t)((depth + nzc - 1) / nzc);
     a.nzc = (int32_t)((depth + a.zchunk - 1) / a.zchunk);
     const int64_t items = cols * a.nzc;

@@ -127,15 +127,6 @@ BS_HD void half_add(uint32_t a, uint32_t b, uint32_t &s, uint32_t &carry)
     carry = a & b;
 }
 
-// Per-voxel count of 4 one-bit inputs as three bit planes (max 4).
-BS_HD void count4(uint32_t a, uint32_t b, uint32_t c, uint32_t d, uint32_t o[3])
-{
-    uint32_t s, c1, c2;
-    full_add(a, b, c, s, c1);
-    half_add(s, d, o[0], c2);
-    half_add(c1, c2, o[1], o[2]);
-}
-
 // Value of a bit-sliced field at bit i.
 template <int K>
 BS_HD int bits_at(const uint32_t *x, int i)
@@ -154,90 +145,92 @@ BS_HD int bits_at(const uint32_t *x, int i)
 // voxel's rival for any cell they share).
 //
 // kappa = sum over cells containing the voxel that it introduces of
-// (-1)^dim = 1 - F + S - C with F faces (6), S squares (12), C cubes (8).
-// Equivalently kappa = T - 13 where T counts the 26 one-bit terms
-// {squares} + {not face} + {not cube} (since 1 - F - C = (6 - F) + (8 - C) - 13).
-// Returns the nonzero mask (T != 13) and the five bit planes of T.
+// (-1)^dim = 1 - F + S - C with F faces won (of 6), S squares (of 12) and C
+// cubes (of 8).  A cell is won when all its edges at the voxel and all its
+// other vertices are, so a cube won implies each of its three squares at
+// the voxel, and a square its two faces.  The 26 signed terms therefore
+// group into chains whose partial sums are single bits:
+//   (1 - f) + s - c  with c => s => f   is  ~f | (s & ~c)    (6 chains)
+//   s - c            with c => s        is  s & ~c           (2 chains)
+//   s                                                        (4 squares)
+// pairing every face, cube and square once (a matching of the cube/square
+// and square/face incidences), so kappa = T - 5 with T the sum of 12 bits,
+// 0 <= T <= 12.  The chain bits cost two logic operations each and T a
+// 12-input carry-save count.
 
-// Per-voxel count of 26 one-bit inputs as five bit planes (max 26).
-BS_HD void count26(const uint32_t x[26], uint32_t o[5])
+// Per-voxel count of 12 one-bit inputs as four bit planes (max 12).
+BS_HD void count12(const uint32_t x[12], uint32_t o[4])
 {
-    uint32_t s[8], c[8];
-#pragma unroll
-    for (int i = 0; i < 8; ++i) full_add(x[3 * i], x[3 * i + 1], x[3 * i + 2], s[i], c[i]);
-    // weight 1: s[0..7], x[24], x[25]
-    uint32_t a0, a1, a2, d0, d1, d2, b0, e0, e1;
-    full_add(s[0], s[1], s[2], a0, d0);
-    full_add(s[3], s[4], s[5], a1, d1);
-    full_add(s[6], s[7], x[24], a2, d2);
-    full_add(a0, a1, a2, b0, e0);
-    half_add(b0, x[25], o[0], e1);
-    // weight 2: c[0..7], d0, d1, d2, e0, e1 (13 terms)
-    uint32_t f[4], g[4];
-    full_add(c[0], c[1], c[2], f[0], g[0]);
-    full_add(c[3], c[4], c[5], f[1], g[1]);
-    full_add(c[6], c[7], d0, f[2], g[2]);
-    full_add(d1, d2, e0, f[3], g[3]);
-    uint32_t h0, k0, k1;
-    full_add(f[0], f[1], f[2], h0, k0);
-    full_add(f[3], e1, h0, o[1], k1);
-    // weight 4: g[0..3], k0, k1 (6 terms)
-    uint32_t m0, n0, m1, n1, n2;
-    full_add(g[0], g[1], g[2], m0, n0);
-    full_add(g[3], k0, k1, m1, n1);
-    half_add(m0, m1, o[2], n2);
-    // weight 8: n0, n1, n2
-    full_add(n0, n1, n2, o[3], o[4]);
+    uint32_t s0, s1, s2, s3, s4, c0, c1, c2, c3, c4, c5;
+    full_add(x[0], x[1], x[2], s0, c0);
+    full_add(x[3], x[4], x[5], s1, c1);
+    full_add(x[6], x[7], x[8], s2, c2);
+    full_add(x[9], x[10], x[11], s3, c3);
+    full_add(s0, s1, s2, s4, c4);
+    half_add(s4, s3, o[0], c5);
+    // weight 2: c0..c5
+    uint32_t s5, s6, d0, d1, d2;
+    full_add(c0, c1, c2, s5, d0);
+    full_add(c3, c4, c5, s6, d1);
+    half_add(s5, s6, o[1], d2);
+    // weight 4: d0, d1, d2
+    full_add(d0, d1, d2, o[2], o[3]);
 }
 
-BS_HD uint32_t kappa3d(const uint32_t w[3][3][3], uint32_t T[5])
+// Returns the nonzero mask (T != 5) and the four bit planes of T.
+BS_HD uint32_t kappa3d(const uint32_t w[3][3][3], uint32_t T[4])
 {
-    const uint32_t ex[2] = {w[1][1][0], w[1][1][2]};
-    const uint32_t ey[2] = {w[1][0][1], w[1][2][1]};
-    const uint32_t ez[2] = {w[0][1][1], w[2][1][1]};
-    uint32_t t[26];
+    const uint32_t ex0 = w[1][1][0], ex1 = w[1][1][2];
+    const uint32_t ey0 = w[1][0][1], ey1 = w[1][2][1];
+    const uint32_t ez0 = w[0][1][1], ez1 = w[2][1][1];
+    // squares sAB[a][b]: side a along the first axis, side b along the second
     uint32_t sxy[2][2], sxz[2][2], syz[2][2];
+    const uint32_t ey[2] = {ey0, ey1}, ex[2] = {ex0, ex1}, ez[2] = {ez0, ez1};
 #pragma unroll
     for (int a = 0; a < 2; ++a)
 #pragma unroll
         for (int b = 0; b < 2; ++b) {
-            sxy[a][b] = ey[a] & ex[b] & w[1][2 * a][2 * b];   // y side a, x side b
-            sxz[a][b] = ez[a] & ex[b] & w[2 * a][1][2 * b];   // z side a, x side b
-            syz[a][b] = ez[a] & ey[b] & w[2 * a][2 * b][1];   // z side a, y side b
-            t[0 + 2 * a + b] = sxy[a][b];
-            t[4 + 2 * a + b] = sxz[a][b];
-            t[8 + 2 * a + b] = syz[a][b];
+            sxy[a][b] = ey[a] & ex[b] & w[1][2 * a][2 * b];
+            sxz[a][b] = ez[a] & ex[b] & w[2 * a][1][2 * b];
+            syz[a][b] = ez[a] & ey[b] & w[2 * a][2 * b][1];
         }
-    t[12] = ~ex[0];
-    t[13] = ~ex[1];
-    t[14] = ~ey[0];
-    t[15] = ~ey[1];
-    t[16] = ~ez[0];
-    t[17] = ~ez[1];
-#pragma unroll
-    for (int c = 0; c < 2; ++c)
-#pragma unroll
-        for (int b = 0; b < 2; ++b)
-#pragma unroll
-            for (int a = 0; a < 2; ++a)   // cube on z side c, y side b, x side a
-                t[18 + 4 * c + 2 * b + a] = ~(sxy[b][a] & sxz[c][a] & syz[c][b] & w[2 * c][2 * b][2 * a]);
-    count26(t, T);
-    // T == 13 = 0b01101
-    return ~(T[0] & ~T[1] & T[2] & T[3] & ~T[4]);
+    // cube (x side a, y side b, z side c) = sxy[b][a] & sxz[c][a] & syz[c][b] & corner;
+    // each chain's cube is its square AND the rest (r) of the cube's condition
+    uint32_t t[12];
+    t[0] = ~ex0 | (sxy[0][0] & ~(sxz[0][0] & syz[0][0] & w[0][0][0]));    // -x, cube (0,0,0)
+    t[1] = ~ex1 | (sxy[1][1] & ~(sxz[0][1] & syz[0][1] & w[0][2][2]));    // +x, cube (1,1,0)
+    t[2] = ~ey0 | (syz[1][0] & ~(sxy[0][0] & sxz[1][0] & w[2][0][0]));    // -y, cube (0,0,1)
+    t[3] = ~ey1 | (syz[0][1] & ~(sxy[1][0] & sxz[0][0] & w[0][2][0]));    // +y, cube (0,1,0)
+    t[4] = ~ez0 | (sxz[0][1] & ~(sxy[0][1] & syz[0][0] & w[0][0][2]));    // -z, cube (1,0,0)
+    t[5] = ~ez1 | (sxz[1][1] & ~(sxy[1][1] & syz[1][1] & w[2][2][2]));    // +z, cube (1,1,1)
+    t[6] = sxy[1][0] & ~(sxz[1][0] & syz[1][1] & w[2][2][0]);             // cube (0,1,1)
+    t[7] = sxy[0][1] & ~(sxz[1][1] & syz[1][0] & w[2][0][2]);             // cube (1,0,1)
+    t[8] = sxz[0][0];
+    t[9] = sxz[1][0];
+    t[10] = syz[0][0];
+    t[11] = syz[1][1];
+    count12(t, T);
+    // T == 5 = 0b0101
+    return ~T[0] | T[1] | ~T[2] | T[3];
 }
 
-// 2D: w[dy+1][dx+1]; kappa = 1 - faces + squares.  Returns the nonzero mask
-// and the planes of F (faces, max 4) and Q (squares, max 4).
-BS_HD uint32_t kappa2d(const uint32_t w[3][3], uint32_t F[3], uint32_t Q[3])
+// 2D: w[dy+1][dx+1]; kappa = 1 - F + Q with F faces (of 4) and Q squares
+// (of 4).  Each face pairs with a square containing it: (1 - f) + q with
+// q => f is the bit ~f | q, so kappa = X[0] + X[1] + 2 X[2] - 3 where
+// X[0] + X[1] + 2 X[2] is the sum of the four chain bits.  Returns the
+// nonzero mask and X.
+BS_HD uint32_t kappa2d(const uint32_t w[3][3], uint32_t X[3])
 {
     const uint32_t ex0 = w[1][0], ex1 = w[1][2], ey0 = w[0][1], ey1 = w[2][1];
-    count4(ex0, ex1, ey0, ey1, F);
-    count4(ey0 & ex0 & w[0][0], ey0 & ex1 & w[0][2], ey1 & ex0 & w[2][0], ey1 & ex1 & w[2][2], Q);
-    // nonzero iff 1 + Q != F (both at most 4, three planes)
-    const uint32_t p0 = ~Q[0], c0 = Q[0];
-    const uint32_t p1 = Q[1] ^ c0, c1 = Q[1] & c0;
-    const uint32_t p2 = Q[2] ^ c1;
-    return (p0 ^ F[0]) | (p1 ^ F[1]) | (p2 ^ F[2]);
+    // square (y side a, x side b) = ey[a] & ex[b] & w[2a][2b]
+    const uint32_t b0 = ~ex0 | (ey0 & w[0][0]);   // -x with square (0,0)
+    const uint32_t b1 = ~ex1 | (ey1 & w[2][2]);   // +x with square (1,1)
+    const uint32_t b2 = ~ey0 | (ex1 & w[0][2]);   // -y with square (0,1)
+    const uint32_t b3 = ~ey1 | (ex0 & w[2][0]);   // +y with square (1,0)
+    full_add(b0, b1, b2, X[0], X[2]);
+    X[1] = b3;
+    // sum == 3 iff X[2] and exactly one of X[0], X[1] (X[0] + X[1] <= 2)
+    return ~(X[2] & (X[0] ^ X[1]));
 }
 
 }  // namespace bs

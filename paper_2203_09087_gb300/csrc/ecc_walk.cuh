@@ -55,6 +55,15 @@ __device__ __forceinline__ uint32_t beats_later(const uint32_t *a, const uint32_
     return TOP ? bs::ge<K>(b, a) : bs::ge<K>(a, b);
 }
 
+// The last carry step of beats_later for one more plane: folds the
+// existence plane (ea of the earlier operand, eb of the later one) into a
+// comparison taken over the value planes.
+template <bool TOP>
+__device__ __forceinline__ uint32_t fold_plane(uint32_t c, uint32_t ea, uint32_t eb)
+{
+    return TOP ? ((eb & ~ea) | ((eb | ~ea) & c)) : ((ea & ~eb) | ((ea | ~eb) & c));
+}
+
 template <int K>
 __device__ __forceinline__ void shifted(const uint32_t *a, uint32_t *p, uint32_t *m)
 {
@@ -140,43 +149,43 @@ struct Bins {
 
 // Emission, per lane: the voxels of mask m (bit i: window element i, value
 // val_at(i)) have nonzero signed counts.  In smooth images 0.4 % of voxels
-// have one and almost all are +-1, so a short per-lane loop of plain
-// atomics beats warp-level aggregation (measured); most warp steps emit
-// nothing at all.
+// have one and almost all are +-1, so most lanes emit nothing in a step and
+// the others one voxel: each lane adds its first +-1 voxel without a loop,
+// and only when some lane has more (or a larger count) does the warp run
+// the per-lane loop.  Warp-collective (all lanes call it).
 //
-// 3D: count = T - 13 from the five bit planes of T (negated for the
-// top-cell complex, (-1)^3); T = 14 and T = 12 (+1 and -1) skip the
-// bit-plane read.
+// 3D: count = T - 5 from the four bit planes of T (negated for the top-cell
+// complex, (-1)^3); T = 6 and T = 4 (+1 and -1) need no bit-plane read.
 template <bool TOP, class ValAt>
 __device__ __forceinline__ void emit_sparse3d(uint32_t m, const uint32_t *T, ValAt &&val_at, const Bins &b)
 {
-    const uint32_t c = T[2] & T[3] & ~T[4] & ~T[0];
-    const uint32_t p1 = m & c & T[1];     // T = 14
-    uint32_t pm = p1 | (m & c & ~T[1]);   // T = 14 or 12
-    uint32_t other = m & ~pm;
-    while (pm) {
+    const uint32_t c = T[2] & ~T[3] & ~T[0];   // T = 4 or 6
+    const uint32_t pm = m & c;
+    uint32_t rest = (m & ~c) | (pm & (pm - 1u));
+    if (pm) {
         const int i = __ffs(pm) - 1;
-        pm &= pm - 1;
-        const int k = ((p1 >> i) & 1u) ? 1 : -1;
+        const int k = ((T[1] >> i) & 1u) ? 1 : -1;
         b.add(val_at(i), TOP ? -k : k);
     }
-    while (other) {
-        const int i = __ffs(other) - 1;
-        other &= other - 1;
-        const int k = bs::bits_at<5>(T, i) - 13;
-        b.add(val_at(i), TOP ? -k : k);
+    if (__any_sync(0xffffffffu, rest != 0u)) {
+        while (rest) {
+            const int i = __ffs(rest) - 1;
+            rest &= rest - 1;
+            const int k = bs::bits_at<4>(T, i) - 5;
+            b.add(val_at(i), TOP ? -k : k);
+        }
     }
 }
 
-// 2D: count = 1 + Q - F ((-1)^2 = +1 in both complexes).
+// 2D: count = X[0] + X[1] + 2 X[2] - 3 ((-1)^2 = +1 in both complexes).
 template <class ValAt>
-__device__ __forceinline__ void emit_sparse2d(uint32_t m, const uint32_t *Q, const uint32_t *F, ValAt &&val_at,
-                                              const Bins &b)
+__device__ __forceinline__ void emit_sparse2d(uint32_t m, const uint32_t *X, ValAt &&val_at, const Bins &b)
 {
     while (m) {
         const int i = __ffs(m) - 1;
         m &= m - 1;
-        b.add(val_at(i), 1 + bs::bits_at<3>(Q, i) - bs::bits_at<3>(F, i));
+        const int k = (int)((X[0] >> i) & 1u) + (int)((X[1] >> i) & 1u) + 2 * (int)((X[2] >> i) & 1u) - 3;
+        b.add(val_at(i), k);
     }
 }
 
@@ -221,55 +230,110 @@ struct Walk3d {
 
     // From plane z (rows a) to plane z+1 (rows b).  When `emit_z`
     // (warp-uniform), calls emit(mask, T, a.P) for plane z: output voxels
-    // with a nonzero count, count = T - 13 before the top-cell sign.
+    // with a nonzero count, count = T - 5 before the top-cell sign.
     // Warp-collective.
     template <class Emit>
     __device__ __forceinline__ void step(const Rows3<K> &a, const Rows3<K> &b, bool emit_z, uint32_t out_x,
                                          Emit &&emit)
     {
-        // plane z against plane z+1 (z earlier): H0[d][x] = A[x-d] vs B[x],
-        // Hp[d][x] = A[x-d] vs Bu[x], K2[d][x] = Au[x] vs B[x+d]
-        uint32_t H0[3], Hp[3], K2[3], E, F[3];
-        {
-            uint32_t Ap[KP], Am[KP];
-            shifted<KP>(a.P, Ap, Am);
-            H0[0] = beats_later<KP, TOP>(Ap, b.P);
-            H0[1] = beats_later<KP, TOP>(a.P, b.P);
-            H0[2] = beats_later<KP, TOP>(Am, b.P);
-            Hp[0] = beats_later<KP, TOP>(Ap, b.U);
-            Hp[1] = beats_later<KP, TOP>(a.P, b.U);
-            Hp[2] = beats_later<KP, TOP>(Am, b.U);
+        // Plane z against plane z+1 (z earlier):
+        //   R0[d][x] = A[x]  vs B[x+d-1]    (z, y)   vs (z+1, y)
+        //   G[d][x]  = D[x]  vs B[x+d-1]    (z, y-1) vs (z+1, y)
+        //   Gu[d][x] = A[x]  vs Bu[x+d-1]   (z, y)   vs (z+1, y+1)  (lane y+1's G)
+        //   K2[d][x] = Au[x] vs B[x+d-1]    (z, y+1) vs (z+1, y)
+        // and the in-plane pairs of plane z+1:
+        //   E[x] = B[x-1] vs B[x],  F[d][x] = B[x+1-d] vs Bu[x].
+        // With 8 planes every shifted operand is a shift of this lane's new
+        // row B: G is taken against D = row y-1 of plane z (from the previous
+        // lane) and Gu is the next lane's G.  With 16 planes plane z is
+        // shifted instead and G is the previous lane's Gu.
+        uint32_t R0[3], G[3], Gu[3], K2[3], E, F[3];
+        // value planes only; the existence plane is folded in below where
+        // some voxel of the two planes is missing (it is zero elsewhere)
+        if constexpr (K == 8) {
+            uint32_t Bp[K], Bm[K], D[K];
+            shifted<K>(b.P, Bp, Bm);
+#pragma unroll
+            for (int k = 0; k < K; ++k) D[k] = from_prev_lane(a.P[k]);
+            R0[0] = beats_later<K, TOP>(a.P, Bm);
+            R0[1] = beats_later<K, TOP>(a.P, b.P);
+            R0[2] = beats_later<K, TOP>(a.P, Bp);
+            G[0] = beats_later<K, TOP>(D, Bm);
+            G[1] = beats_later<K, TOP>(D, b.P);
+            G[2] = beats_later<K, TOP>(D, Bp);
+            K2[0] = beats_later<K, TOP>(a.U, Bm);
+            K2[1] = beats_later<K, TOP>(a.U, b.P);
+            K2[2] = beats_later<K, TOP>(a.U, Bp);
+            E = beats_later<K, TOP>(Bm, b.P);
+            F[0] = beats_later<K, TOP>(Bp, b.U);
+            F[1] = beats_later<K, TOP>(b.P, b.U);
+            F[2] = beats_later<K, TOP>(Bm, b.U);
+        } else {
+            // 16 planes: shifting plane z costs less than shuffling the 16
+            // planes of row y-1 would; Gu is this lane's own comparison with
+            // row y+1 and G the previous lane's
+            {
+                uint32_t Ap[K], Am[K];
+                shifted<K>(a.P, Ap, Am);
+                R0[0] = at_offset<-1>(beats_later<K, TOP>(Ap, b.P));   // A[x] vs B[x-1]
+                R0[1] = beats_later<K, TOP>(a.P, b.P);
+                R0[2] = at_offset<+1>(beats_later<K, TOP>(Am, b.P));   // A[x] vs B[x+1]
+                Gu[0] = at_offset<-1>(beats_later<K, TOP>(Ap, b.U));
+                Gu[1] = beats_later<K, TOP>(a.P, b.U);
+                Gu[2] = at_offset<+1>(beats_later<K, TOP>(Am, b.U));
+            }
+            uint32_t Bp[K], Bm[K];
+            shifted<K>(b.P, Bp, Bm);
+            K2[0] = beats_later<K, TOP>(a.U, Bm);
+            K2[1] = beats_later<K, TOP>(a.U, b.P);
+            K2[2] = beats_later<K, TOP>(a.U, Bp);
+            E = beats_later<K, TOP>(Bm, b.P);
+            F[0] = beats_later<K, TOP>(Bp, b.U);
+            F[1] = beats_later<K, TOP>(b.P, b.U);
+            F[2] = beats_later<K, TOP>(Bm, b.U);
         }
-        {
-            uint32_t Bp[KP], Bm[KP];
-            shifted<KP>(b.P, Bp, Bm);
-            K2[0] = beats_later<KP, TOP>(a.U, Bm);
-            K2[1] = beats_later<KP, TOP>(a.U, b.P);
-            K2[2] = beats_later<KP, TOP>(a.U, Bp);
-            // in-plane pairs of plane z+1: E[x] = B[x-1] vs B[x], F[d][x] = B[x-d] vs Bu[x]
-            E = beats_later<KP, TOP>(Bm, b.P);
-            F[0] = beats_later<KP, TOP>(Bp, b.U);
-            F[1] = beats_later<KP, TOP>(b.P, b.U);
-            F[2] = beats_later<KP, TOP>(Bm, b.U);
+        if (__any_sync(0xffffffffu, (a.P[K] | b.P[K]) != 0u)) {
+            const uint32_t eB = b.P[K], eBp = shr1(eB), eBm = shl1(eB), eA = a.P[K];
+            const uint32_t eAu = a.U[K], eBu = b.U[K];
+            R0[0] = fold_plane<TOP>(R0[0], eA, eBm);
+            R0[1] = fold_plane<TOP>(R0[1], eA, eB);
+            R0[2] = fold_plane<TOP>(R0[2], eA, eBp);
+            if constexpr (K == 8) {
+                const uint32_t eD = from_prev_lane(eA);
+                G[0] = fold_plane<TOP>(G[0], eD, eBm);
+                G[1] = fold_plane<TOP>(G[1], eD, eB);
+                G[2] = fold_plane<TOP>(G[2], eD, eBp);
+            } else {
+                Gu[0] = fold_plane<TOP>(Gu[0], eA, shl1(eBu));
+                Gu[1] = fold_plane<TOP>(Gu[1], eA, eBu);
+                Gu[2] = fold_plane<TOP>(Gu[2], eA, shr1(eBu));
+            }
+            K2[0] = fold_plane<TOP>(K2[0], eAu, eBm);
+            K2[1] = fold_plane<TOP>(K2[1], eAu, eB);
+            K2[2] = fold_plane<TOP>(K2[2], eAu, eBp);
+            E = fold_plane<TOP>(E, eBm, eB);
+            F[0] = fold_plane<TOP>(F[0], eBp, eBu);
+            F[1] = fold_plane<TOP>(F[1], eB, eBu);
+            F[2] = fold_plane<TOP>(F[2], eBm, eBu);
         }
-        uint32_t Hp_dn[3], K2_dn[3], F_dn[3];
+        uint32_t K2_dn[3], F_dn[3];
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-            Hp_dn[d] = from_prev_lane(Hp[d]);
-            K2_dn[d] = from_prev_lane(K2[d]);
+            if constexpr (K == 8)
+                Gu[d] = from_next_lane(G[d]);   // lane y+1's G: (z, y) vs (z+1, y+1)
+            else
+                G[d] = from_prev_lane(Gu[d]);   // lane y-1's Gu: (z, y-1) vs (z+1, y)
+            K2_dn[d] = from_prev_lane(K2[d]);   // lane y-1's K2: (z, y) vs (z+1, y-1)
             F_dn[d] = from_prev_lane(F[d]);
         }
         if (emit_z) {
             uint32_t w[3][3][3];
-            w[2][1][0] = at_offset<-1>(H0[0]);
-            w[2][1][1] = H0[1];
-            w[2][1][2] = at_offset<+1>(H0[2]);
-            w[2][2][0] = at_offset<-1>(Hp[0]);
-            w[2][2][1] = Hp[1];
-            w[2][2][2] = at_offset<+1>(Hp[2]);
-            w[2][0][0] = K2_dn[0];   // row y-1 of z+1 at x-1: lane y-1's Au (= our A) vs its B[x-1]
-            w[2][0][1] = K2_dn[1];
-            w[2][0][2] = K2_dn[2];
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                w[2][1][d] = R0[d];
+                w[2][2][d] = Gu[d];
+                w[2][0][d] = K2_dn[d];
+            }
 #pragma unroll
             for (int dy = 0; dy < 3; ++dy)
 #pragma unroll
@@ -282,20 +346,20 @@ struct Walk3d {
                 w[1][0][dx] = wym[dx];
                 w[1][2][dx] = wyp[dx];
             }
-            uint32_t T[5];
+            uint32_t T[4];
             const uint32_t m = bs::kappa3d(w, T) & out_x;
             emit(m, T, a.P);
         }
         // wins of (z+1, y) over plane z (an earlier neighbour wins ties)
-        Wm[1][0] = ~H0[2];
-        Wm[1][1] = ~H0[1];
-        Wm[1][2] = ~H0[0];
+        Wm[1][0] = ~at_offset<-1>(R0[2]);
+        Wm[1][1] = ~R0[1];
+        Wm[1][2] = ~at_offset<+1>(R0[0]);
         Wm[2][0] = ~at_offset<-1>(K2[2]);
         Wm[2][1] = ~K2[1];
         Wm[2][2] = ~at_offset<+1>(K2[0]);
-        Wm[0][0] = ~Hp_dn[2];
-        Wm[0][1] = ~Hp_dn[1];
-        Wm[0][2] = ~Hp_dn[0];
+        Wm[0][0] = ~at_offset<-1>(G[2]);
+        Wm[0][1] = ~G[1];
+        Wm[0][2] = ~at_offset<+1>(G[0]);
         // in-plane wins of (z+1, y)
         wx2 = at_offset<+1>(E);
         wx0 = ~E;
@@ -328,7 +392,7 @@ struct Walk2d {
     }
 
     // Advance to row y+1 (window B).  yp: row y+1 exists; y_ok: row y exists.
-    // When emit_y, calls emit(mask, Q, F, A) for row y with count = 1 + Q - F.
+    // When emit_y, calls emit(mask, X, A) for row y with count = X0 + X1 + 2 X2 - 3.
     template <class Emit>
     __device__ __forceinline__ void step(const uint32_t *B, bool yp, bool y_ok, bool emit_y, uint32_t out_x,
                                          Emit &&emit)
@@ -356,9 +420,9 @@ struct Walk2d {
             w[2][0] = with_exist<TOP>(at_offset<-1>(H[0]), ey_p & ex_x[0]);
             w[2][1] = with_exist<TOP>(H[1], ey_p);
             w[2][2] = with_exist<TOP>(at_offset<+1>(H[2]), ey_p & ex_x[2]);
-            uint32_t F[3], Q[3];
-            const uint32_t m = bs::kappa2d(w, F, Q) & out_x;
-            emit(m, Q, F, A);
+            uint32_t X[3];
+            const uint32_t m = bs::kappa2d(w, X) & out_x;
+            emit(m, X, A);
         }
 #pragma unroll
         for (int dx = 0; dx < 3; ++dx) wym[dx] = with_exist<TOP>(~H[2 - dx], ey_m1 & ex_x[dx]);

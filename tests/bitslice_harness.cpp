@@ -13,7 +13,7 @@ void h_transpose_u16(const uint32_t *r, uint32_t *p) { transpose_u16(r, p); }
 uint32_t h_ge8(const uint32_t *a, const uint32_t *b) { return ge<8>(a, b); }
 uint32_t h_ge16(const uint32_t *a, const uint32_t *b) { return ge<16>(a, b); }
 
-// w: 27 masks in [dz][dy][dx] order; writes T[5] (kappa = T - 13); returns nonzero mask
+// w: 27 masks in [dz][dy][dx] order; writes T[4] (kappa = T - 5); returns nonzero mask
 uint32_t h_kappa3d(const uint32_t *w27, uint32_t *T)
 {
     uint32_t w[3][3][3];
@@ -21,13 +21,25 @@ uint32_t h_kappa3d(const uint32_t *w27, uint32_t *T)
     return kappa3d(w, T);
 }
 
-void h_count26(const uint32_t *x, uint32_t *o) { count26(x, o); }
+// n words per input: w27[i * n + j] is input i of word j; T[k * n + j], nz[j]
+void h_kappa3d_many(const uint32_t *w27, int64_t n, uint32_t *T, uint32_t *nz)
+{
+    for (int64_t j = 0; j < n; ++j) {
+        uint32_t w[3][3][3], t[4];
+        for (int i = 0; i < 27; ++i) w[i / 9][(i / 3) % 3][i % 3] = w27[i * n + j];
+        nz[j] = kappa3d(w, t);
+        for (int k = 0; k < 4; ++k) T[k * n + j] = t[k];
+    }
+}
 
-uint32_t h_kappa2d(const uint32_t *w9, uint32_t *F, uint32_t *Q)
+void h_count12(const uint32_t *x, uint32_t *o) { count12(x, o); }
+
+// w: 9 masks in [dy][dx] order; writes X[3] (kappa = X0 + X1 + 2 X2 - 3); returns nonzero mask
+uint32_t h_kappa2d(const uint32_t *w9, uint32_t *X)
 {
     uint32_t w[3][3];
     for (int i = 0; i < 9; ++i) w[i / 3][i % 3] = w9[i];
-    return kappa2d(w, F, Q);
+    return kappa2d(w, X);
 }
 
 }

@@ -19,14 +19,15 @@ def h(tmp_path_factory):
                     str(ROOT / "tests" / "bitslice_harness.cpp"), "-o", str(out)], check=True)
     lib = ctypes.CDLL(str(out))
     u32p = ctypes.POINTER(ctypes.c_uint32)
-    for n in ("h_transpose_u8", "h_transpose_u16", "h_count26"):
+    for n in ("h_transpose_u8", "h_transpose_u16", "h_count12"):
         getattr(lib, n).argtypes = [u32p, u32p]
     for n in ("h_ge8", "h_ge16"):
         getattr(lib, n).argtypes = [u32p, u32p]
         getattr(lib, n).restype = ctypes.c_uint32
     lib.h_kappa3d.argtypes = [u32p, u32p]
     lib.h_kappa3d.restype = ctypes.c_uint32
-    lib.h_kappa2d.argtypes = [u32p, u32p, u32p]
+    lib.h_kappa2d.argtypes = [u32p, u32p]
+    lib.h_kappa3d_many.argtypes = [u32p, ctypes.c_int64, u32p, u32p]
     lib.h_kappa2d.restype = ctypes.c_uint32
     return lib
 
@@ -80,15 +81,16 @@ def _vals(planes, nbits):
     return [sum(((int(planes[k]) >> x) & 1) << k for k in range(nbits)) for x in range(32)]
 
 
-@pytest.mark.parametrize("n,fn", [(26, "h_count26")])
-def test_counters(h, n, fn):
+@pytest.mark.parametrize("n,fn,planes", [(12, "h_count12", 4)])
+def test_counters(h, n, fn, planes):
     rng = np.random.default_rng(3)
-    for _ in range(300):
-        x = rng.integers(0, 1 << 32, size=n, dtype=np.uint64).astype(np.uint32)
-        o = np.zeros(5, np.uint32)
-        getattr(h, fn)(_p(x), _p(o))
-        want = [sum((int(x[i]) >> b) & 1 for i in range(n)) for b in range(32)]
-        assert _vals(o, 5) == want
+    for density in (0.1, 0.5, 0.9, 1.0):
+        for _ in range(100):
+            x = np.array([sum(int(rng.uniform() < density) << b for b in range(32)) for _ in range(n)], np.uint32)
+            o = np.zeros(planes, np.uint32)
+            getattr(h, fn)(_p(x), _p(o))
+            want = [sum((int(x[i]) >> b) & 1 for i in range(n)) for b in range(32)]
+            assert _vals(o, planes) == want
 
 
 def kappa3d_scalar(w):
@@ -114,14 +116,56 @@ def test_kappa3d(h):
         for _ in range(40):
             bits = (rng.uniform(size=(27, 32)) < density).astype(np.uint64)
             w27 = np.array([sum(int(bits[i, x]) << x for x in range(32)) for i in range(27)], np.uint32)
-            T = np.zeros(5, np.uint32)
+            T = np.zeros(4, np.uint32)
             nz = h.h_kappa3d(_p(w27), _p(T))
-            t = _vals(T, 5)
+            t = _vals(T, 4)
             for x in range(32):
                 w = bits[:, x].reshape(3, 3, 3).astype(int)
                 kap = kappa3d_scalar(w)
-                assert t[x] - 13 == kap
+                assert t[x] - 5 == kap
                 assert ((nz >> x) & 1) == (kap != 0)
+
+
+def test_kappa3d_exhaustive(h):
+    """The chain grouping of the signed cell count is an identity of the 26
+    win bits: check every one of the 2^26 win patterns against
+    1 - faces + squares - cubes evaluated term by term."""
+    n_cfg = 1 << 26
+    words = n_cfg // 32
+    j = np.arange(words, dtype=np.uint32)
+    # input bit b of configuration 32*j + x is bit b of that index
+    win_idx = [i for i in range(27) if i != 13]           # skip the centre
+    w27 = np.zeros((27, words), np.uint32)
+    low = [np.uint32(sum(1 << x for x in range(32) if (x >> b) & 1)) for b in range(5)]
+    for b, i in enumerate(win_idx):
+        w27[i] = low[b] if b < 5 else np.where((j >> (b - 5)) & 1, np.uint32(0xFFFFFFFF), np.uint32(0))
+    T = np.zeros((4, words), np.uint32)
+    nz = np.zeros(words, np.uint32)
+    h.h_kappa3d_many(_p(w27), words, _p(T), _p(nz))
+    # reference: per configuration, from the index bits (in chunks)
+    bit = lambda arr: ((arr[:, None] >> np.arange(32, dtype=np.uint32)) & 1).reshape(-1).astype(np.int8)
+    chunk = 1 << 22
+    for c0 in range(0, n_cfg, chunk):
+        cfg = np.arange(c0, c0 + chunk, dtype=np.uint32)
+        wb = {i: ((cfg >> b) & 1).astype(np.int8) for b, i in enumerate(win_idx)}
+        W = lambda dz, dy, dx: wb[9 * dz + 3 * dy + dx]
+        kap = np.ones(chunk, np.int8)
+        for f in [(0, 1, 1), (2, 1, 1), (1, 0, 1), (1, 2, 1), (1, 1, 0), (1, 1, 2)]:
+            kap -= W(*f)
+        for a in (0, 2):
+            for b in (0, 2):
+                kap += W(1, a, 1) & W(1, 1, b) & W(1, a, b)
+                kap += W(a, 1, 1) & W(1, 1, b) & W(a, 1, b)
+                kap += W(a, 1, 1) & W(1, b, 1) & W(a, b, 1)
+        for c in (0, 2):
+            for b in (0, 2):
+                for a in (0, 2):
+                    kap -= (W(c, 1, 1) & W(1, b, 1) & W(1, 1, a) & W(c, b, 1) & W(c, 1, a) & W(1, b, a)
+                            & W(c, b, a))
+        sl = slice(c0 // 32, (c0 + chunk) // 32)
+        t = bit(T[0, sl]) + 2 * bit(T[1, sl]) + 4 * bit(T[2, sl]) + 8 * bit(T[3, sl])
+        assert np.array_equal(t - 5, kap)
+        assert np.array_equal(bit(nz[sl]), (kap != 0).astype(np.int8))
 
 
 def test_kappa2d(h):
@@ -130,15 +174,14 @@ def test_kappa2d(h):
         for _ in range(60):
             bits = (rng.uniform(size=(9, 32)) < density).astype(np.uint64)
             w9 = np.array([sum(int(bits[i, x]) << x for x in range(32)) for i in range(9)], np.uint32)
-            F = np.zeros(3, np.uint32)
-            Q = np.zeros(3, np.uint32)
-            nz = h.h_kappa2d(_p(w9), _p(F), _p(Q))
-            f, q = _vals(F, 3), _vals(Q, 3)
+            X = np.zeros(3, np.uint32)
+            nz = h.h_kappa2d(_p(w9), _p(X))
             for x in range(32):
+                xs = [(int(X[j]) >> x) & 1 for j in range(3)]
                 w = bits[:, x].reshape(3, 3).astype(int)
                 kap = 1 - (w[1, 0] + w[1, 2] + w[0, 1] + w[2, 1])
                 for a in (0, 2):
                     for b in (0, 2):
                         kap += w[a, 1] & w[1, b] & w[a, b]
-                assert 1 - f[x] + q[x] == kap
+                assert xs[0] + xs[1] + 2 * xs[2] - 3 == kap
                 assert ((nz >> x) & 1) == (kap != 0)
