@@ -142,6 +142,28 @@ ecc_status ecc_compute(ecc_plan_t plan, const ecc_image *img, int64_t *d_ecc,
  * ecc_compute plus ECC_E_RANGE (device errors are checked before return). */
 ecc_status ecc_compute_host(ecc_plan_t plan, const ecc_image *h_img, int64_t *h_ecc, void *stream);
 
+/* Out-of-core ECC of a HOST image of any size (Sec. 3.4, Fig. 5: the
+ * streaming that lets the paper process volumes larger than device memory).
+ * The image is cut along dims[0] into chunks; each chunk travels with a
+ * one-slab collar on each side that exists into one of three device
+ * buffers taken from the plan (allocated on first use, kept until
+ * ecc_plan_destroy), so the device holds at most device_budget_bytes of
+ * image data (0 = 1 GiB) whatever the image size.  The copy of a chunk (on
+ * the plan's copy stream) overlaps the stencil of the previous one (on
+ * `stream`); the stencil of a chunk emits only its own slabs and reads the
+ * collar as neighbours, so the result equals ecc_compute on the whole
+ * image.
+ *   h_img     host image; may exceed the plan's max_voxels and the device
+ *             memory.  Pinned memory gives overlapped copies.
+ *   h_ecc     host int64[nbins], written before return.
+ * Synchronous: returns when h_ecc is written.  Errors: ECC_E_INVALID
+ * (including a budget below three buffers of three slabs, one slab being
+ * dims[1] rows in 3D or one row in 2D, rows padded to 16 bytes),
+ * ECC_E_NOMEM (the chunk buffers could not be allocated), ECC_E_RANGE,
+ * ECC_E_TIMEOUT, ECC_E_CUDA. */
+ecc_status ecc_compute_stream(ecc_plan_t plan, const ecc_image *h_img, int64_t *h_ecc,
+                              int64_t device_budget_bytes, void *stream);
+
 /* ECC of n images of arbitrary, uneven shapes in ONE persistent kernel that
  * walks a device-side tile work list (per-image histogram offsets), launched
  * through a CUDA graph captured once per plan, followed by one segmented

@@ -8,6 +8,7 @@ memory and streams only.  The functions keep the C names:
     ecc = ecc_compute(plan, volume_cuda_tensor)         # ecc_compute
     eccs = ecc_compute_batch(plan, [img0, img1, ...])   # ecc_compute_batch
     ecc_host = ecc_compute_host(plan, numpy_array)      # ecc_compute_host
+    ecc_big = ecc_compute_stream(plan, huge_array, 1 << 30)  # ecc_compute_stream (out of core)
     srv = ecc_server_create(budget_bytes, n_streams=4)  # ecc_server_create / ecc_submit / ...
 
 There is no CPU fallback: importing works anywhere, but the first call loads
@@ -41,6 +42,7 @@ from ._binding import (  # noqa: F401
     ecc_compute,
     ecc_compute_batch,
     ecc_compute_host,
+    ecc_compute_stream,
     ecc_compute_noalloc,
     ecc_last_error,
     ecc_plan,

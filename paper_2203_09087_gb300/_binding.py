@@ -60,6 +60,7 @@ _SIGNATURES = {
     "ecc_compute": (ctypes.c_int, [_VP, ctypes.POINTER(EccImage), _VP, _VP, _VP]),
     "ecc_compute_host": (ctypes.c_int, [_VP, ctypes.POINTER(EccImage), _VP, _VP]),
     "ecc_compute_batch": (ctypes.c_int, [_VP, _I32, ctypes.POINTER(EccImage), _VP, _VP]),
+    "ecc_compute_stream": (ctypes.c_int, [_VP, ctypes.POINTER(EccImage), _VP, _I64, _VP]),
     "ecc_compute_noalloc": (ctypes.c_int, [ctypes.POINTER(EccImage), _I32, _I32, _I32, ctypes.c_uint32, _VP, _VP,
                                            _VP]),
     "ecc_status_get": (ctypes.c_int, [_VP, _VP]),
@@ -254,6 +255,20 @@ def ecc_compute_host(plan: Plan, array: np.ndarray, out: np.ndarray | None = Non
     if out.dtype != np.int64 or not out.flags.c_contiguous or out.size < plan.nbins:
         raise ValueError("out must be a contiguous int64 array")
     _check(library().ecc_compute_host(plan.handle, ctypes.byref(d), out.ctypes.data, _stream_handle(stream)))
+    return out
+
+
+def ecc_compute_stream(plan: Plan, array: np.ndarray, device_budget_bytes: int = 0, out: np.ndarray | None = None,
+                       stream=None) -> np.ndarray:
+    """Out-of-core ECC of a host array of any size through at most ``device_budget_bytes`` of device
+    chunk buffers (0 = 1 GiB); returns a host int64 array."""
+    d = host_image_desc(array)
+    if out is None:
+        out = np.empty(plan.nbins, dtype=np.int64)
+    if out.dtype != np.int64 or not out.flags.c_contiguous or out.size < plan.nbins:
+        raise ValueError("out must be a contiguous int64 array")
+    _check(library().ecc_compute_stream(plan.handle, ctypes.byref(d), out.ctypes.data, int(device_budget_bytes),
+                                        _stream_handle(stream)))
     return out
 
 

@@ -333,4 +333,90 @@ ecc_status ecc_compute_host(ecc_plan_t p, const ecc_image *h_img, int64_t *h_ecc
     return ecc_status_get(p, stream);
 }
 
+ecc_status ecc_compute_stream(ecc_plan_t p, const ecc_image *h_img, int64_t *h_ecc, int64_t device_budget_bytes,
+                              void *stream)
+{
+    if (!p) return invalid("ecc_compute_stream: NULL plan");
+    if (!h_ecc) return invalid("ecc_compute_stream: NULL output");
+    if (device_budget_bytes < 0) return invalid("ecc_compute_stream: negative device budget");
+    Geom hg;
+    int64_t nvox = 0;
+    // any size: the image never has to fit the device or the plan's max_voxels
+    ecc_status st = image_geom(h_img, p->d.dtype, 0, &hg, &nvox, false);
+    if (st != ECC_OK) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int64_t budget = device_budget_bytes ? device_budget_bytes : (int64_t(1) << 30);
+
+    // Chunks along the outer axis (Sec. 3.4, Fig. 5).  A chunk of C outer
+    // slabs travels with a one-slab collar on each side that exists, into
+    // one of kRing device buffers; the stencil of chunk k emits only its own
+    // slabs and reads the collar as real neighbours, while the image's own
+    // boundary stays a boundary.  Device rows are padded to 16 bytes so
+    // every chunk takes the TMA kernel.
+    const int64_t dpitch_y = (hg.nx * hg.esize + 15) / 16 * 16;
+    const int64_t outer = hg.ndim == 3 ? hg.nz : hg.ny;
+    const int64_t slab = hg.ndim == 3 ? hg.ny * dpitch_y : dpitch_y;   // bytes of one outer slab
+    const int64_t per_buf = budget / kRing / 256 * 256;
+    if (per_buf / slab < 3) {
+        set_error("ecc_compute_stream: device budget below three buffers of three slabs (one slab plus collar)");
+        return ECC_E_INVALID;
+    }
+    const int64_t C = std::min<int64_t>(per_buf / slab - 2, outer);
+    const int64_t buf_bytes = (C + 2) * slab;
+    const int64_t buf_stride = (buf_bytes + 255) / 256 * 256;
+    st = p->ensure_ring(buf_stride * kRing);
+    if (st != ECC_OK) return st;
+
+    p->last_launches = 0;
+    cudaError_t e = cudaSuccess;
+    HistDst h{p->acc, p->d.lo, p->nbins};
+    if (p->d.flags & ECC_FLAG_COUNT_EMITTED) h.emitted = p->emitted;
+    const unsigned char *src = static_cast<const unsigned char *>(h_img->data);
+    const int64_t nchunks = (outer + C - 1) / C;
+    for (int64_t k = 0; k < nchunks && e == cudaSuccess; ++k) {
+        const int64_t c0 = k * C, c1 = std::min(c0 + C, outer);
+        const int64_t base = c0 > 0 ? c0 - 1 : 0, top = c1 < outer ? c1 + 1 : outer;
+        const int b = (int)(k % kRing);
+        unsigned char *buf = p->ring + b * buf_stride;
+        // the buffer is free once the stencil that last read it has run
+        if (k >= kRing) e = cudaStreamWaitEvent(p->copy_stream, p->ring_done[b], 0);
+        if (e == cudaSuccess) {
+            if (hg.ndim == 3 && hg.pitch_z == hg.ny * hg.pitch_y)   // slabs contiguous: one copy
+                e = cudaMemcpy2DAsync(buf, dpitch_y, src + base * hg.pitch_z, hg.pitch_y, hg.nx * hg.esize,
+                                      (top - base) * hg.ny, cudaMemcpyHostToDevice, p->copy_stream);
+            else if (hg.ndim == 3)
+                for (int64_t z = base; z < top && e == cudaSuccess; ++z)
+                    e = cudaMemcpy2DAsync(buf + (z - base) * slab, dpitch_y, src + z * hg.pitch_z, hg.pitch_y,
+                                          hg.nx * hg.esize, hg.ny, cudaMemcpyHostToDevice, p->copy_stream);
+            else
+                e = cudaMemcpy2DAsync(buf, dpitch_y, src + base * hg.pitch_y, hg.pitch_y, hg.nx * hg.esize,
+                                      top - base, cudaMemcpyHostToDevice, p->copy_stream);
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(p->ring_copied[b], p->copy_stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(s, p->ring_copied[b], 0);
+        if (e == cudaSuccess) {
+            Geom v = hg;
+            v.data = buf;
+            v.pitch_y = dpitch_y;
+            if (hg.ndim == 3) {
+                v.nz = top - base;
+                v.pitch_z = slab;
+            } else {
+                v.ny = top - base;
+                v.pitch_z = v.ny * dpitch_y;
+            }
+            e = launch_stencil(p, v, c0 - base, c1 - base, h, s);
+        }
+        if (e == cudaSuccess) e = cudaEventRecord(p->ring_done[b], s);
+    }
+    if (e == cudaSuccess) {
+        e = launch_scan(p->acc, p->stage_ecc, nullptr, 1, p->nbins, p->scan_ws(), p->status, s);
+        ++p->last_launches;
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h_ecc, p->stage_ecc, sizeof(int64_t) * p->nbins, cudaMemcpyDeviceToHost, s);
+    if (e != cudaSuccess) return cuda_fail(e, "ecc_compute_stream");
+    return ecc_status_get(p, stream);
+}
+
 }  // extern "C"

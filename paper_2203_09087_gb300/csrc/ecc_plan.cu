@@ -67,12 +67,46 @@ ecc_status ecc_plan_s::ensure_stage(int64_t bytes)
     return ECC_OK;
 }
 
+ecc_status ecc_plan_s::ensure_ring(int64_t bytes)
+{
+    // the streams, events and ECC staging of the host-input path come first
+    ecc_status st = ensure_stage(0);
+    if (st != ECC_OK) return st;
+    if (!ring_copied[0]) {
+        cudaError_t e = cudaSuccess;
+        for (int i = 0; i < kRing && e == cudaSuccess; ++i) {
+            e = cudaEventCreateWithFlags(&ring_copied[i], cudaEventDisableTiming);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ring_done[i], cudaEventDisableTiming);
+        }
+        if (e != cudaSuccess) return cuda_fail(e, "ecc_compute_stream: event setup");
+    }
+    if ((size_t)bytes > ring_bytes) {
+        if (ring) cudaFree(ring);
+        ring = nullptr;
+        ring_bytes = 0;
+        cudaError_t e = cudaMalloc(&ring, (size_t)bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            set_error("ecc_compute_stream: device chunk buffers allocation failed");
+            return ECC_E_NOMEM;
+        }
+        ring_bytes = (size_t)bytes;
+    }
+    return ECC_OK;
+}
+
 void ecc_plan_s::release()
 {
     if (batch) release_batch(this);
     if (ws) cudaFree(ws);
     if (stage) cudaFree(stage);
+    if (ring) cudaFree(ring);
     if (stage_ecc) cudaFree(stage_ecc);
+    for (int i = 0; i < kRing; ++i) {
+        if (ring_copied[i]) cudaEventDestroy(ring_copied[i]);
+        if (ring_done[i]) cudaEventDestroy(ring_done[i]);
+        ring_copied[i] = ring_done[i] = nullptr;
+    }
     for (int i = 0; i < kMaxChunkEvents; ++i)
         if (chunk_ev[i]) cudaEventDestroy(chunk_ev[i]);
     for (cudaEvent_t ev : time_ev) cudaEventDestroy(ev);
@@ -80,6 +114,8 @@ void ecc_plan_s::release()
     if (copy_stream) cudaStreamDestroy(copy_stream);
     ws = nullptr;
     stage = nullptr;
+    ring = nullptr;
+    ring_bytes = 0;
     stage_ecc = nullptr;
     copy_stream = nullptr;
 }

@@ -11,6 +11,7 @@
 namespace ecc {
 
 constexpr int kMaxChunkEvents = 16;
+constexpr int kRing = 3;  // device chunk buffers of the out-of-core path
 
 struct BatchState;  // ecc_batch.cu
 
@@ -42,6 +43,13 @@ struct ecc_plan_s {
     cudaStream_t copy_stream = nullptr;
     cudaEvent_t chunk_ev[ecc::kMaxChunkEvents] = {};
 
+    // out-of-core streaming (ecc_compute_stream): one allocation split into
+    // kRing chunk buffers, with "copied" and "consumed" events per buffer
+    unsigned char *ring = nullptr;
+    size_t ring_bytes = 0;
+    cudaEvent_t ring_copied[ecc::kRing] = {};
+    cudaEvent_t ring_done[ecc::kRing] = {};
+
     // tile parameter per (ndim, esize) key chosen by the autotuner
     int tuned[4] = {0, 0, 0, 0};
     // batch path: rows per 2D tile, planes per 3D tile (0 = default)
@@ -57,6 +65,7 @@ struct ecc_plan_s {
     void release();
     void autotune();
     ecc_status ensure_stage(int64_t bytes);
+    ecc_status ensure_ring(int64_t bytes);
     int tune_param(const ecc::Geom &g) const;
     ecc::ScanWs scan_ws() const
     {
