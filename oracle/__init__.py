@@ -72,6 +72,11 @@ def _declare(lib):
         f.restype = ctypes.c_int
     lib.oracle_ecc_from_vcec.argtypes = [i64p, ctypes.c_int64, i64p]
     lib.oracle_ecc_from_vcec.restype = None
+    for name in ("oracle_levels_vertex_rows", "oracle_levels_topcell_rows"):
+        f = getattr(lib, name)
+        f.argtypes = [ctypes.c_void_p, ctypes.c_int, i64p, ctypes.c_int64, ctypes.c_int64,
+                      ctypes.POINTER(ctypes.c_double), ctypes.c_int64, i64p]
+        f.restype = ctypes.c_int
     return lib
 
 
@@ -148,6 +153,49 @@ def vcec_rows(img: np.ndarray, begin: int, end: int, lo=None, hi=None, mode: str
     _check(fn(img.ctypes.data, _dtype_code(img), img.ndim, _i64p(dims), int(begin), int(end),
               lo, hi, _i64p(out)))
     return out
+
+
+def level_bins_rows(img: np.ndarray, levels, begin: int, end: int, mode: str = VERTEX, lib=None) -> np.ndarray:
+    """Signed cell counts of a float32 image per threshold index (int64[m]):
+    bin i holds the cells whose value's first level at or above it is
+    levels[i] (Eq. 1 with the t_i given), for the dims[0] indices in
+    [begin, end).  Disjoint ranges add up."""
+    lib = lib or load()
+    img = np.ascontiguousarray(img, dtype=np.float32)
+    lv = np.ascontiguousarray(levels, dtype=np.float64)
+    dims = np.asarray(img.shape, dtype=np.int64)
+    out = np.zeros(lv.size, dtype=np.int64)
+    fn = lib.oracle_levels_vertex_rows if mode == VERTEX else lib.oracle_levels_topcell_rows
+    _check(fn(img.ctypes.data, img.ndim, _i64p(dims), int(begin), int(end),
+              lv.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), lv.size, _i64p(out)))
+    return out
+
+
+def ecc_levels(img: np.ndarray, levels, mode: str = VERTEX, threads: int = 1) -> np.ndarray:
+    """ECC of a float32 image at ascending thresholds: int64[m], entry i =
+    chi(K_{<= levels[i]}).  NaN voxels count as +infinity."""
+    lib = load()
+    img = np.ascontiguousarray(img, dtype=np.float32)
+    end = row_extent(img.shape, mode)
+    threads = max(1, min(threads, end))
+    cuts = np.linspace(0, end, threads + 1).round().astype(np.int64)
+    parts = [None] * threads
+    errors = []
+
+    def work(i):
+        try:
+            parts[i] = level_bins_rows(img, levels, cuts[i], cuts[i + 1], mode, lib)
+        except Exception as e:  # surfaced below
+            errors.append(e)
+
+    ts = [threading.Thread(target=work, args=(i,)) for i in range(threads)]
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join()
+    if errors:
+        raise errors[0]
+    return ecc_from_vcec(np.sum(parts, axis=0).astype(np.int64), lib)
 
 
 def row_extent(img_shape, mode: str = VERTEX) -> int:

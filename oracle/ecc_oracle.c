@@ -53,6 +53,7 @@
 #include <stdint.h>
 #include <stddef.h>
 #include <string.h>
+#include <math.h>
 
 #define ORACLE_MAX_DIM 4
 
@@ -209,4 +210,114 @@ void oracle_ecc_from_vcec(const int64_t *vcec, int64_t nbins, int64_t *ecc)
         run += vcec[g];
         ecc[g] = run;
     }
+}
+
+/*
+ * Thresholds on float32 images (Eq. 1 with the levels t_i given).
+ *
+ * ECC_i = chi(K_{<= t_i}) = sum over cells sigma with value(sigma) <= t_i of
+ * (-1)^dim(sigma), for ascending levels t_0 <= ... <= t_{m-1}.  Each cell is
+ * enumerated exactly as above, its value computed in floating point (max of
+ * its vertices, or min of its top cofaces), and (-1)^dim added to bin i =
+ * the first index whose level is >= the value; a cell above t_{m-1} lies in
+ * no sublevel set and is skipped.  The prefix sum of the m bins is then the
+ * ECC at the m thresholds.  A NaN voxel counts as +infinity.
+ */
+static double float_value(const float *img, int64_t lin)
+{
+    const double v = (double)img[lin];
+    return v != v ? (double)INFINITY : v;
+}
+
+/* First index i in [0, m] with levels[i] >= v (m if none). */
+static int64_t first_level_at_or_above(const double *levels, int64_t m, double v)
+{
+    int64_t lo = 0, hi = m;
+    while (lo < hi) {
+        const int64_t mid = lo + (hi - lo) / 2;
+        if (levels[mid] < v) lo = mid + 1; else hi = mid;
+    }
+    return lo;
+}
+
+int oracle_levels_vertex_rows(const float *img, int ndim, const int64_t *dims, int64_t row_begin, int64_t row_end,
+                              const double *levels, int64_t m, int64_t *bins)
+{
+    if (!img || !dims || !levels || !bins || m < 1 || ndim < 1 || ndim > ORACLE_MAX_DIM) return 1;
+    for (int a = 0; a < ndim; ++a)
+        if (dims[a] < 1) return 1;
+    for (int64_t i = 1; i < m; ++i)
+        if (!(levels[i - 1] <= levels[i])) return 1;
+    if (row_begin < 0 || row_end > dims[0] || row_begin > row_end) return 1;
+    if (row_begin == row_end) return 0;
+
+    int64_t lo_a[ORACLE_MAX_DIM], hi_a[ORACLE_MAX_DIM], p[ORACLE_MAX_DIM];
+    for (int a = 0; a < ndim; ++a) { lo_a[a] = 0; hi_a[a] = dims[a]; p[a] = 0; }
+    lo_a[0] = row_begin; hi_a[0] = row_end; p[0] = row_begin;
+
+    const unsigned n_subsets = 1u << ndim;
+    do {
+        for (unsigned A = 0; A < n_subsets; ++A) {
+            int exists = 1, dim = 0;
+            for (int a = 0; a < ndim; ++a) {
+                if (A & (1u << a)) {
+                    ++dim;
+                    if (p[a] + 1 >= dims[a]) exists = 0;
+                }
+            }
+            if (!exists) continue;
+            double value = -(double)INFINITY;
+            for (unsigned B = 0; B < n_subsets; ++B) {
+                if (B & ~A) continue;
+                int64_t q[ORACLE_MAX_DIM];
+                for (int a = 0; a < ndim; ++a) q[a] = p[a] + ((B >> a) & 1u);
+                const double v = float_value(img, linear_index(ndim, dims, q));
+                if (v > value) value = v;
+            }
+            const int64_t i = first_level_at_or_above(levels, m, value);
+            if (i < m) bins[i] += (dim % 2 == 0) ? 1 : -1;
+        }
+    } while (next_coord(ndim, lo_a, hi_a, p));
+    return 0;
+}
+
+int oracle_levels_topcell_rows(const float *img, int ndim, const int64_t *dims, int64_t e_begin, int64_t e_end,
+                               const double *levels, int64_t m, int64_t *bins)
+{
+    if (!img || !dims || !levels || !bins || m < 1 || ndim < 1 || ndim > ORACLE_MAX_DIM) return 1;
+    for (int a = 0; a < ndim; ++a)
+        if (dims[a] < 1) return 1;
+    for (int64_t i = 1; i < m; ++i)
+        if (!(levels[i - 1] <= levels[i])) return 1;
+    if (e_begin < 0 || e_end > 2 * dims[0] + 1 || e_begin > e_end) return 1;
+    if (e_begin == e_end) return 0;
+
+    int64_t lo_a[ORACLE_MAX_DIM], hi_a[ORACLE_MAX_DIM], e[ORACLE_MAX_DIM];
+    for (int a = 0; a < ndim; ++a) { lo_a[a] = 0; hi_a[a] = 2 * dims[a] + 1; e[a] = 0; }
+    lo_a[0] = e_begin; hi_a[0] = e_end; e[0] = e_begin;
+
+    do {
+        int64_t first[ORACLE_MAX_DIM], last[ORACLE_MAX_DIM];
+        int dim = 0;
+        for (int a = 0; a < ndim; ++a) {
+            int64_t k = e[a] / 2;
+            if (e[a] % 2 == 1) {
+                ++dim;
+                first[a] = k; last[a] = k;
+            } else {
+                first[a] = (k - 1 < 0) ? 0 : k - 1;
+                last[a] = (k > dims[a] - 1) ? dims[a] - 1 : k;
+            }
+        }
+        double value = (double)INFINITY;
+        int64_t v_hi[ORACLE_MAX_DIM], q[ORACLE_MAX_DIM];
+        for (int a = 0; a < ndim; ++a) { q[a] = first[a]; v_hi[a] = last[a] + 1; }
+        do {
+            const double v = float_value(img, linear_index(ndim, dims, q));
+            if (v < value) value = v;
+        } while (next_coord(ndim, first, v_hi, q));
+        const int64_t i = first_level_at_or_above(levels, m, value);
+        if (i < m) bins[i] += (dim % 2 == 0) ? 1 : -1;
+    } while (next_coord(ndim, lo_a, hi_a, e));
+    return 0;
 }

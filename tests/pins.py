@@ -112,3 +112,11 @@ def symmetries(img: np.ndarray):
                 if f:
                     u = np.flip(u, axis=a)
             yield np.ascontiguousarray(u)
+
+
+def bruteforce_ecc_levels(img: np.ndarray, levels, mode: str) -> np.ndarray:
+    """The naive method at given thresholds of a float image (Eq. 1 with the
+    t_i given): threshold at each level and count cells.  A NaN voxel is at
+    no level, i.e. above all of them."""
+    count = _vertex_cell_counts if mode == "vertex" else _topcell_cell_counts
+    return np.array([count(img <= t) for t in levels], dtype=np.int64)
