@@ -66,7 +66,9 @@ typedef enum {
     ECC_E_CANCELLED = 8   /* the job was cancelled before it ran */
 } ecc_status;
 
-typedef enum { ECC_U8 = 1, ECC_U16 = 2 } ecc_dtype;
+/* ECC_F32: float32 images, accepted only by ecc_compute_levels (plans are
+ * ECC_U8 or ECC_U16). */
+typedef enum { ECC_U8 = 1, ECC_U16 = 2, ECC_F32 = 3 } ecc_dtype;
 
 typedef enum { ECC_VERTEX_MAX = 0, ECC_TOPCELL_MIN = 1 } ecc_complex;
 
@@ -141,6 +143,27 @@ ecc_status ecc_compute(ecc_plan_t plan, const ecc_image *img, int64_t *d_ecc,
  * memory gives the fastest copies; pageable memory works.  Errors as
  * ecc_compute plus ECC_E_RANGE (device errors are checked before return). */
 ecc_status ecc_compute_host(ecc_plan_t plan, const ecc_image *h_img, int64_t *h_ecc, void *stream);
+
+/* ECC of a float32 image at m given thresholds (Eq. 1 with the t_i given:
+ * ECC_i = chi(K_{<= t_i})), asynchronously on `stream`.  The paper's
+ * datasets are float32 and its kernel bins values as integers (Algorithm
+ * 2); here each voxel is mapped to the number of levels strictly below it
+ * (NaN: above every level) -- a monotone map, so a cell is in K_{<= t_i}
+ * exactly when its mapped value is <= i -- into a copy in the plan's
+ * staging memory, and the integer stencil and scan follow.
+ *   plan      ECC_U8 (m <= 255) or ECC_U16 plan with lo = 0 and hi >= m;
+ *             its max_voxels bounds the image; the copy is 1 (ECC_U8) or 2
+ *             bytes per voxel, allocated on first use.
+ *   img       device image, dtype ECC_F32, 4-byte aligned pitches.
+ *   d_levels  device float[m], ascending (ties allowed; the order is
+ *             checked on the device).
+ *   d_ecc     device int64[m], written: d_ecc[i] = chi(K_{<= d_levels[i]}).
+ * No host synchronization.  Errors returned directly: ECC_E_INVALID,
+ * ECC_E_BUSY (more voxels than max_voxels), ECC_E_NOMEM, ECC_E_CUDA;
+ * through ecc_status_get: ECC_E_INVALID (levels not ascending),
+ * ECC_E_TIMEOUT. */
+ecc_status ecc_compute_levels(ecc_plan_t plan, const ecc_image *img, const float *d_levels, int32_t m,
+                              int64_t *d_ecc, void *stream);
 
 /* Out-of-core ECC of a HOST image of any size (Sec. 3.4, Fig. 5: the
  * streaming that lets the paper process volumes larger than device memory).

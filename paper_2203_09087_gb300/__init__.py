@@ -9,6 +9,7 @@ memory and streams only.  The functions keep the C names:
     eccs = ecc_compute_batch(plan, [img0, img1, ...])   # ecc_compute_batch
     ecc_host = ecc_compute_host(plan, numpy_array)      # ecc_compute_host
     ecc_big = ecc_compute_stream(plan, huge_array, 1 << 30)  # ecc_compute_stream (out of core)
+    ecc_t = ecc_compute_levels(plan_u16, f32_tensor, levels)  # ecc_compute_levels (float thresholds)
     srv = ecc_server_create(budget_bytes, n_streams=4)  # ecc_server_create / ecc_submit / ...
 
 There is no CPU fallback: importing works anywhere, but the first call loads
@@ -35,6 +36,7 @@ from ._binding import (  # noqa: F401
     ECC_TOPCELL_MIN,
     ECC_U8,
     ECC_U16,
+    ECC_F32,
     ECC_VERTEX_MAX,
     EccError,
     Plan,
@@ -42,6 +44,7 @@ from ._binding import (  # noqa: F401
     ecc_compute,
     ecc_compute_batch,
     ecc_compute_host,
+    ecc_compute_levels,
     ecc_compute_stream,
     ecc_compute_noalloc,
     ecc_last_error,

@@ -13,7 +13,7 @@ _HEADER = _PKG.parent / "include" / "ecc.h"
 
 ECC_OK, ECC_E_INVALID, ECC_E_RANGE, ECC_E_NOMEM, ECC_E_CUDA = 0, 1, 2, 3, 4
 ECC_E_TIMEOUT, ECC_E_BUSY, ECC_E_SHUTDOWN, ECC_E_CANCELLED = 5, 6, 7, 8
-ECC_U8, ECC_U16 = 1, 2
+ECC_U8, ECC_U16, ECC_F32 = 1, 2, 3
 ECC_VERTEX_MAX, ECC_TOPCELL_MIN = 0, 1
 ECC_FLAG_NO_RANGE_CHECK = 0x1
 ECC_FLAG_NO_AUTOTUNE = 0x2
@@ -61,6 +61,7 @@ _SIGNATURES = {
     "ecc_compute_host": (ctypes.c_int, [_VP, ctypes.POINTER(EccImage), _VP, _VP]),
     "ecc_compute_batch": (ctypes.c_int, [_VP, _I32, ctypes.POINTER(EccImage), _VP, _VP]),
     "ecc_compute_stream": (ctypes.c_int, [_VP, ctypes.POINTER(EccImage), _VP, _I64, _VP]),
+    "ecc_compute_levels": (ctypes.c_int, [_VP, ctypes.POINTER(EccImage), _VP, _I32, _VP, _VP]),
     "ecc_compute_noalloc": (ctypes.c_int, [ctypes.POINTER(EccImage), _I32, _I32, _I32, ctypes.c_uint32, _VP, _VP,
                                            _VP]),
     "ecc_status_get": (ctypes.c_int, [_VP, _VP]),
@@ -255,6 +256,26 @@ def ecc_compute_host(plan: Plan, array: np.ndarray, out: np.ndarray | None = Non
     if out.dtype != np.int64 or not out.flags.c_contiguous or out.size < plan.nbins:
         raise ValueError("out must be a contiguous int64 array")
     _check(library().ecc_compute_host(plan.handle, ctypes.byref(d), out.ctypes.data, _stream_handle(stream)))
+    return out
+
+
+def ecc_compute_levels(plan: Plan, image, levels, out=None, stream=None):
+    """ECC of a float32 CUDA image at the ascending thresholds ``levels`` (a float32 CUDA
+    tensor of m entries); returns the int64 CUDA tensor ``out`` of m entries."""
+    import torch
+    if image.dtype != torch.float32 or levels.dtype != torch.float32:
+        raise TypeError("image and levels must be float32 tensors")
+    if not image.is_cuda or not levels.is_cuda:
+        raise ValueError("image and levels must be CUDA tensors")
+    if not levels.is_contiguous() or levels.dim() != 1:
+        raise ValueError("levels must be a contiguous 1-D tensor")
+    m = levels.numel()
+    d = _desc(image.data_ptr(), image.dim(), ECC_F32, tuple(image.shape), tuple(image.stride()), 4)
+    if out is None:
+        out = torch.empty(m, dtype=torch.int64, device=image.device)
+    _check_out(out, m)
+    _check(library().ecc_compute_levels(plan.handle, ctypes.byref(d), levels.data_ptr(), m, out.data_ptr(),
+                                        _stream_handle(stream)))
     return out
 
 

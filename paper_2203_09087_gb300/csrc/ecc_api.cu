@@ -26,7 +26,7 @@ ecc_status cuda_fail(cudaError_t e, const char *what)
     return ECC_E_CUDA;
 }
 
-static ecc_status invalid(const std::string &msg)
+ecc_status invalid(const std::string &msg)
 {
     set_error(msg);
     return ECC_E_INVALID;
@@ -38,7 +38,8 @@ ecc_status image_geom(const ecc_image *img, int32_t want_dtype, int64_t max_voxe
     if (!img) return invalid("image descriptor is NULL");
     if (!img->data && !allow_null_data) return invalid("image data pointer is NULL");
     if (img->ndim != 2 && img->ndim != 3) return invalid("ndim must be 2 or 3");
-    if (img->dtype != ECC_U8 && img->dtype != ECC_U16) return invalid("dtype must be ECC_U8 or ECC_U16");
+    if (img->dtype != ECC_U8 && img->dtype != ECC_U16 && !(img->dtype == ECC_F32 && want_dtype == ECC_F32))
+        return invalid("dtype must be ECC_U8 or ECC_U16 (ECC_F32 only through ecc_compute_levels)");
     if (want_dtype && img->dtype != want_dtype) return invalid("image dtype differs from the plan's dtype");
     int64_t n = 1;
     for (int a = 0; a < img->ndim; ++a) {
@@ -47,7 +48,7 @@ ecc_status image_geom(const ecc_image *img, int32_t want_dtype, int64_t max_voxe
         n *= img->dims[a];
         if (n > (int64_t(1) << 40)) return invalid("image too large");
     }
-    const int es = img->dtype == ECC_U16 ? 2 : 1;
+    const int es = img->dtype == ECC_F32 ? 4 : (img->dtype == ECC_U16 ? 2 : 1);
     Geom r{};
     r.data = static_cast<const unsigned char *>(img->data);
     r.ndim = img->ndim;
@@ -259,6 +260,10 @@ ecc_status ecc_status_get(ecc_plan_t p, void *stream)
     if (word & DEV_RANGE) {
         set_error("an image value lies outside [lo, hi]");
         return ECC_E_RANGE;
+    }
+    if (word & DEV_LEVELS) {
+        set_error("the threshold levels are not in ascending order");
+        return ECC_E_INVALID;
     }
     return ECC_OK;
 }

@@ -15,6 +15,7 @@ namespace ecc {
 enum : uint32_t {
     DEV_RANGE = 1u,    // an image value outside [lo, hi]
     DEV_TIMEOUT = 2u,  // a bounded spin-wait gave up
+    DEV_LEVELS = 4u,   // threshold levels not in ascending order
 };
 
 // Upper bound for every device-side spin-wait (nanoseconds of %globaltimer).
@@ -103,5 +104,6 @@ int64_t scan_tiles(int64_t n_seg, int32_t nbins);
 
 void set_error(const std::string &msg);
 ecc_status cuda_fail(cudaError_t e, const char *what);
+ecc_status invalid(const std::string &msg);  // sets the message, returns ECC_E_INVALID
 
 }  // namespace ecc
