@@ -39,6 +39,7 @@ from ._binding import (  # noqa: F401
     ECC_F32,
     ECC_VERTEX_MAX,
     EccError,
+    ImageDescs,
     Plan,
     Server,
     ecc_compute,
@@ -62,6 +63,7 @@ from ._binding import (  # noqa: F401
     ecc_submit,
     ecc_wait,
     exported_symbols,
+    image_descs,
     library,
     library_path,
 )

@@ -293,15 +293,35 @@ def ecc_compute_stream(plan: Plan, array: np.ndarray, device_budget_bytes: int =
     return out
 
 
+class ImageDescs:
+    """A reusable array of ecc_image descriptors for ecc_compute_batch.
+
+    Building one descriptor per tensor costs host time per image; a caller
+    that runs the same images repeatedly builds the array once.  The
+    descriptors hold the tensors' addresses, shapes and strides at build
+    time: the tensors must stay alive and keep their storage."""
+
+    def __init__(self, images):
+        self.images = list(images)   # keeps the tensors alive
+        self.n = len(self.images)
+        self.array = (EccImage * self.n)(*[image_desc(t) for t in self.images])
+        self.device = self.images[0].device if self.n else None
+
+
+def image_descs(images) -> ImageDescs:
+    return ImageDescs(images)
+
+
 def ecc_compute_batch(plan: Plan, images, out=None, stream=None):
-    """ECC of every image in ``images`` (CUDA tensors, mixed shapes); returns int64 [n, nbins]."""
+    """ECC of every image in ``images`` (CUDA tensors of mixed shapes, or an
+    ImageDescs built from them); returns int64 [n, nbins]."""
     import torch
-    n = len(images)
-    descs = (EccImage * n)(*[image_desc(t) for t in images])
+    descs = images if isinstance(images, ImageDescs) else ImageDescs(images)
+    n = descs.n
     if out is None:
-        out = torch.empty((n, plan.nbins), dtype=torch.int64, device=images[0].device)
+        out = torch.empty((n, plan.nbins), dtype=torch.int64, device=descs.device)
     _check_out(out, n * plan.nbins)
-    _check(library().ecc_compute_batch(plan.handle, n, descs, out.data_ptr(), _stream_handle(stream)))
+    _check(library().ecc_compute_batch(plan.handle, n, descs.array, out.data_ptr(), _stream_handle(stream)))
     return out
 
 

@@ -6,8 +6,10 @@
 //
 //  1. the host packs one descriptor per image into pinned staging memory;
 //  2. a one-CTA kernel turns the descriptors into a device-side work list:
-//     per image, its number of tiles (2D: 960 columns x `chunk` rows; 3D:
-//     30x30 voxels x `chunk` planes) and the exclusive prefix of the counts;
+//     per image, its number of tiles (2D: 32 pairs of a 30-column window and
+//     a `chunk`-row range, one per lane, so narrow images still fill a warp;
+//     3D: 30x30 voxels x `chunk` planes) and the exclusive prefix of the
+//     counts;
 //  3. the persistent kernel's warps pull tiles from an atomic counter, find
 //     their image by binary search over the prefix, and walk the tile with the
 //     bit-sliced walkers (ecc_walk.cuh), reading rows straight from global
@@ -66,7 +68,6 @@ struct BatchState {
 namespace {
 
 constexpr int kBatchWarps = 4;
-constexpr int kTile2d = 32 * 30;  // columns per 2D tile (one warp of windows)
 constexpr int kOut3 = 30;         // x and y extent of a 3D tile
 
 struct BatchArgs {
@@ -84,9 +85,10 @@ struct BatchArgs {
 __device__ __forceinline__ long long tiles_of(const BatchImage &im, int chunk2d, int chunk3d)
 {
     if (im.ndim == 2) {
-        const long long tx = (im.nx + kTile2d - 1) / kTile2d;
+        // 32 (window, row-chunk) pairs per tile, one per lane
+        const long long nwin = (im.nx + 29) / 30;
         const long long ty = (im.ny + chunk2d - 1) / chunk2d;
-        return tx * ty;
+        return (nwin * ty + 31) / 32;
     }
     const long long tx = (im.nx + kOut3 - 1) / kOut3;
     const long long ty = (im.ny + kOut3 - 1) / kOut3;
@@ -143,11 +145,18 @@ __device__ void run_tile(const BatchArgs &a, const BatchImage &im, long long loc
     constexpr int NWORDS = K;
     const int64_t row_bytes = im.nx * (K / 8);
     if (ND == 2) {
-        const long long tx = (im.nx + kTile2d - 1) / kTile2d;
-        const int64_t xt = local % tx, yc = local / tx;
+        // Lane l walks pair q = 32 local + l: window q mod nwin of row chunk
+        // q / nwin.  The 2D walker needs nothing from other lanes (each
+        // window carries its own one-voxel halo), so lanes may walk
+        // different rows and narrow images still fill the warp.
+        const long long nwin = (im.nx + 29) / 30;
+        const long long ty = (im.ny + a.chunk2d - 1) / a.chunk2d;
+        const long long q = 32 * local + lane;
+        if (q >= nwin * ty) return;
+        const int64_t yc = q / nwin, xt = q - yc * nwin;
         const int64_t yb = yc * a.chunk2d;
         const int64_t ye = yb + a.chunk2d < im.ny ? yb + a.chunk2d : im.ny;
-        const int64_t xw = xt * kTile2d + 30 * lane - 1;
+        const int64_t xw = 30 * xt - 1;
         const int64_t first = xw * (K / 8);
         const uint32_t xex = walk::x_exist_mask(xw, im.nx);
         const uint32_t out_x = xex & 0x7ffffffeu;
@@ -239,7 +248,7 @@ __device__ void run_tile(const BatchArgs &a, const BatchImage &im, long long loc
 }
 
 template <int K, bool TOP>
-__global__ void __launch_bounds__(kBatchWarps * 32, 1) batch_kernel(BatchArgs a)
+__global__ void __launch_bounds__(kBatchWarps * 32, 4) batch_kernel(BatchArgs a)
 {
     extern __shared__ __align__(16) int bhist[];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -250,6 +259,7 @@ __global__ void __launch_bounds__(kBatchWarps * 32, 1) batch_kernel(BatchArgs a)
     const int n = a.hdr->n;
     const long long total = a.start[n];
     int cur = -1;  // image whose bins this warp's shared histogram holds
+    long long cur_begin = 0, cur_end = 0;  // its tile range
     auto flush = [&]() {
         if (hist && cur >= 0) {
             __syncwarp();
@@ -269,8 +279,14 @@ __global__ void __launch_bounds__(kBatchWarps * 32, 1) batch_kernel(BatchArgs a)
         if (lane == 0) item = (long long)atomicAdd(a.counter, 1u);
         item = __shfl_sync(0xffffffffu, item, 0);
         if (item >= total) break;
-        // image owning this tile: last i with start[i] <= item
+        // image owning this tile: last i with start[i] <= item (tiles are
+        // handed out in image order, so it is usually the warp's last image)
         int lo = 0, hi = n - 1;
+        if (cur >= 0 && item >= cur_begin && item < cur_end) {
+            lo = hi = cur;
+        } else if (cur >= 0 && item >= cur_end) {
+            lo = cur + 1;
+        }
         while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
             if (a.start[mid] <= item)
@@ -281,6 +297,8 @@ __global__ void __launch_bounds__(kBatchWarps * 32, 1) batch_kernel(BatchArgs a)
         if (lo != cur) {
             flush();
             cur = lo;
+            cur_begin = a.start[lo];
+            cur_end = a.start[lo + 1];
         }
         const BatchImage im = a.img[lo];
         const walk::Bins em{hist, a.acc + (size_t)lo * a.nbins, a.lo, a.nbins, a.range_check, a.status};
