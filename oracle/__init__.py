@@ -231,3 +231,46 @@ def vcec_parallel(img: np.ndarray, lo=None, hi=None, mode: str = VERTEX, threads
     if errors:
         raise errors[0]
     return np.sum(parts, axis=0).astype(np.int64)
+
+
+def reflect_index(j: np.ndarray, n: int) -> np.ndarray:
+    """Half-sample symmetric reflection of indices into [0, n): ... 1 0 | 0 1 ... n-1 | n-1 n-2 ..."""
+    p = np.mod(j, 2 * n)
+    return np.where(p >= n, 2 * n - 1 - p, p)
+
+
+def blur_axis(img: np.ndarray, weights: np.ndarray, axis: int) -> np.ndarray:
+    """One pass of a discrete convolution along `axis` in float32 (the
+    smoothing step of the paper's iterated ECC + Gaussian pipeline, Sec. 4
+    "GPU-only pipeline"): out[x] = sum over taps k = -r..r, in that order, of
+    w[k + r] * in[reflect(x + k)], every product and partial sum rounded to
+    float32 (no fused multiply-add)."""
+    img = np.asarray(img, np.float32)
+    w = np.asarray(weights, np.float32)
+    r = (w.size - 1) // 2
+    n = img.shape[axis]
+    acc = np.zeros_like(img, dtype=np.float32)
+    for k in range(-r, r + 1):
+        idx = reflect_index(np.arange(n) + k, n)
+        term = np.take(img, idx, axis=axis) * w[k + r]          # float32 product
+        acc = (acc + term).astype(np.float32)                    # float32 sum
+    return acc
+
+
+def blur(img: np.ndarray, weights) -> np.ndarray:
+    """Separable smoothing: one pass per axis, last axis first."""
+    out = np.asarray(img, np.float32)
+    for axis in range(out.ndim - 1, -1, -1):
+        out = blur_axis(out, weights, axis)
+    return out
+
+
+def gaussian_pipeline(img: np.ndarray, weights, levels, iterations: int, mode: str = VERTEX, threads: int = 1):
+    """The iterated pipeline: ECC at the levels, then smooth, `iterations`
+    times.  Returns (int64[iterations, m] ECCs, final image)."""
+    cur = np.asarray(img, np.float32)
+    eccs = []
+    for _ in range(iterations):
+        eccs.append(ecc_levels(cur, levels, mode, threads))
+        cur = blur(cur, weights)
+    return np.stack(eccs), cur
