@@ -368,6 +368,44 @@ def run_float_levels(args):
                     "frac": alg / (ms * 1e-3) / 1e9 / peak, "peak_source": src}}
 
 
+def run_gaussian_pipeline(args):
+    """The paper's GPU-only pipeline (Table 2): a 1024^2 float32 Gaussian
+    random field resident on the device, (ECC at 256 levels, then 13-tap
+    separable Gaussian smoothing) repeated 1, 10, 100 and 1000 times through
+    ecc_pipeline_gaussian (rounds of four or more run as one captured CUDA
+    graph launched per round).  Whole-call time from CUDA events."""
+    import numpy as np
+    import torch
+
+    import paper_2203_09087_gb300 as ecc
+    import synth
+    g = torch.Generator(device="cuda")
+    g.manual_seed(5)
+    base = synth.smooth(torch.randn((1024, 1024), generator=g, device="cuda"), 3.0).contiguous()
+    levels = torch.linspace(float(base.min()), float(base.max()), 256, device="cuda").float().contiguous()
+    taps = ecc.gaussian_taps(2.0)
+    plan = ecc.ecc_plan("u16", 0, 256, max_voxels=base.numel())
+    img = base.clone()
+    ecc.ecc_pipeline_gaussian(plan, img, taps, 5, levels)   # warm-up
+    ecc.ecc_status_get(plan)
+    rows = {}
+    for n in (1, 10, 100, 1000):
+        img.copy_(base)
+        out = torch.empty((n, 256), dtype=torch.int64, device="cuda")
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record()
+        ecc.ecc_pipeline_gaussian(plan, img, taps, n, levels, out=out)
+        b.record()
+        torch.cuda.synchronize()
+        ecc.ecc_status_get(plan)
+        ms = a.elapsed_time(b)
+        rows[f"x{n}"] = {"overall_ms": ms, "per_iteration_ms": ms / n}
+        assert int(out[0, -1].item()) == 1
+    return {"workload": "1024^2 float32 Gaussian random field (sigma 3, seed 5), 256 levels, 13-tap Gaussian "
+                        "(sigma 2), (ECC + smoothing) x n on the device", "rounds": rows}
+
+
 def run_serving(args):
     """Poisson stream of mixed 2D/3D uint8/uint16 requests (crops of resident
     seeded fields): p50/p99 latency at the nominal rate, and throughput of a
@@ -584,6 +622,7 @@ def main():
         line["batched"] = run_batched(args)
         line["single_u16"] = run_single_u16(args)
         line["float_levels"] = run_float_levels(args)
+        line["gaussian_pipeline"] = run_gaussian_pipeline(args)
         line["serving"] = run_serving(args)
     if rank == 0:
         print(json.dumps(line))

@@ -165,6 +165,28 @@ ecc_status ecc_compute_host(ecc_plan_t plan, const ecc_image *h_img, int64_t *h_
 ecc_status ecc_compute_levels(ecc_plan_t plan, const ecc_image *img, const float *d_levels, int32_t m,
                               int64_t *d_ecc, void *stream);
 
+/* The paper's GPU-only pipeline (Sec. 4 "GPU-only pipeline", Table 2): a
+ * float32 image resident on the device goes through `iterations` rounds of
+ * (1) its ECC at the m thresholds d_levels (exactly ecc_compute_levels) and
+ * (2) a separable smoothing filter applied in place, one pass per axis,
+ * last axis first, with the given taps (the paper uses a 13-tap Gaussian):
+ * out[x] = sum over k = -r..r, in that order, of taps[k + r] * in[x + k]
+ * along the axis, with half-sample symmetric reflection at the borders
+ * (in[-1] = in[0], in[n] = in[n-1]) and float32 rounding after every
+ * multiply and every add (no fused multiply-add), so any implementation
+ * with the same order reproduces it bit for bit.
+ *   plan       as for ecc_compute_levels; also holds a float32 scratch
+ *              copy of the image (allocated on first use).
+ *   img        device ECC_F32 image, smoothed in place: on return it has
+ *              been filtered `iterations` times.
+ *   h_taps     host float[ntaps], ntaps odd, at most 33 (copied).
+ *   d_ecc      device int64[iterations][m]: row i is the ECC of the image
+ *              after i filter rounds.
+ * Asynchronous on `stream`.  Errors as ecc_compute_levels. */
+ecc_status ecc_pipeline_gaussian(ecc_plan_t plan, const ecc_image *img, const float *h_taps, int32_t ntaps,
+                                 int32_t iterations, const float *d_levels, int32_t m, int64_t *d_ecc,
+                                 void *stream);
+
 /* Out-of-core ECC of a HOST image of any size (Sec. 3.4, Fig. 5: the
  * streaming that lets the paper process volumes larger than device memory).
  * The image is cut along dims[0] into chunks; each chunk travels with a

@@ -62,6 +62,7 @@ _SIGNATURES = {
     "ecc_compute_batch": (ctypes.c_int, [_VP, _I32, ctypes.POINTER(EccImage), _VP, _VP]),
     "ecc_compute_stream": (ctypes.c_int, [_VP, ctypes.POINTER(EccImage), _VP, _I64, _VP]),
     "ecc_compute_levels": (ctypes.c_int, [_VP, ctypes.POINTER(EccImage), _VP, _I32, _VP, _VP]),
+    "ecc_pipeline_gaussian": (ctypes.c_int, [_VP, ctypes.POINTER(EccImage), _VP, _I32, _I32, _VP, _I32, _VP, _VP]),
     "ecc_compute_noalloc": (ctypes.c_int, [ctypes.POINTER(EccImage), _I32, _I32, _I32, ctypes.c_uint32, _VP, _VP,
                                            _VP]),
     "ecc_status_get": (ctypes.c_int, [_VP, _VP]),
@@ -276,6 +277,33 @@ def ecc_compute_levels(plan: Plan, image, levels, out=None, stream=None):
     _check_out(out, m)
     _check(library().ecc_compute_levels(plan.handle, ctypes.byref(d), levels.data_ptr(), m, out.data_ptr(),
                                         _stream_handle(stream)))
+    return out
+
+
+def gaussian_taps(sigma: float, radius: int = 6) -> np.ndarray:
+    """Normalized float32 Gaussian taps (2 radius + 1 of them; the paper's filter has 13)."""
+    k = np.arange(-radius, radius + 1, dtype=np.float64)
+    w = np.exp(-0.5 * (k / float(sigma)) ** 2)
+    return (w / w.sum()).astype(np.float32)
+
+
+def ecc_pipeline_gaussian(plan: Plan, image, taps, iterations: int, levels, out=None, stream=None):
+    """Iterated (ECC at ``levels``, then smoothing with ``taps``) on a float32 CUDA image,
+    in place; returns the int64 CUDA tensor [iterations, m] of ECCs."""
+    import torch
+    if image.dtype != torch.float32 or levels.dtype != torch.float32:
+        raise TypeError("image and levels must be float32 tensors")
+    if not image.is_cuda or not levels.is_cuda:
+        raise ValueError("image and levels must be CUDA tensors")
+    taps = np.ascontiguousarray(taps, dtype=np.float32)
+    m = levels.numel()
+    d = _desc(image.data_ptr(), image.dim(), ECC_F32, tuple(image.shape), tuple(image.stride()), 4)
+    if out is None:
+        out = torch.empty((int(iterations), m), dtype=torch.int64, device=image.device)
+    _check_out(out, int(iterations) * m)
+    _check(library().ecc_pipeline_gaussian(plan.handle, ctypes.byref(d), taps.ctypes.data, taps.size,
+                                           int(iterations), levels.data_ptr(), m, out.data_ptr(),
+                                           _stream_handle(stream)))
     return out
 
 

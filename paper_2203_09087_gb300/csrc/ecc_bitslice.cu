@@ -503,7 +503,12 @@ cudaError_t launch_2d_t(const Geom &g, int64_t yb, int64_t ye, const HistDst &h,
     const int64_t warps_max = (int64_t)num_sms * per_sm_cached * kWarps2d;
     const int64_t depth = ye - yb;
     int64_t nyc = (3 * warps_max + a.ntx - 1) / a.ntx;
-    if (nyc > (depth + 15) / 16) nyc = (depth + 15) / 16;
+    // chunks of at least 16 rows (each re-reads one halo row), unless that
+    // leaves fewer than four warps per SM: small images walk 4-row chunks
+    // (a warp's walk is a chain of dependent row steps)
+    const int64_t cap16 = (depth + 15) / 16, cap4 = (depth + 3) / 4;
+    const int64_t cap = cap16 * a.ntx >= 4 * (int64_t)num_sms ? cap16 : cap4;
+    if (nyc > cap) nyc = cap;
     if (nyc < 1) nyc = 1;
     a.ychunk = (int32_t)((depth + nyc - 1) / nyc);
     a.nyc = (int32_t)((depth + a.ychunk - 1) / a.ychunk);

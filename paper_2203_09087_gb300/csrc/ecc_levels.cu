@@ -140,29 +140,32 @@ cudaError_t launch_quantize_any(const QuantArgs &a, int64_t blocks, cudaStream_t
 }  // namespace
 }  // namespace ecc
 
-using namespace ecc;
+namespace ecc {
 
-extern "C" ecc_status ecc_compute_levels(ecc_plan_t p, const ecc_image *img, const float *d_levels, int32_t m,
-                                         int64_t *d_ecc, void *stream)
+// Checks a float32 image and level count against the plan and sizes the
+// staging copy; on success fills the image's geometry.
+ecc_status levels_prepare(ecc_plan_s *p, const ecc_image *img, int32_t m, Geom *g)
 {
-    if (!p) return invalid("ecc_compute_levels: NULL plan");
-    if (!d_levels || !d_ecc) return invalid("ecc_compute_levels: NULL levels or output");
     if (m < 1 || m > 65535) return invalid("ecc_compute_levels: the number of levels must be in [1, 65535]");
     if (p->d.lo != 0 || p->d.hi < m)
         return invalid("ecc_compute_levels: the plan must cover levels [0, m] (lo = 0, hi >= m)");
-    Geom g;
     int64_t nvox = 0;
-    ecc_status st = image_geom(img, ECC_F32, p->d.max_voxels, &g, &nvox, false);
+    ecc_status st = image_geom(img, ECC_F32, p->d.max_voxels, g, &nvox, false);
     if (st != ECC_OK) return st;
-    if (reinterpret_cast<uintptr_t>(g.data) % 4 || g.pitch_y % 4 || g.pitch_z % 4)
+    if (reinterpret_cast<uintptr_t>(g->data) % 4 || g->pitch_y % 4 || g->pitch_z % 4)
         return invalid("ecc_compute_levels: float32 image must be 4-byte aligned");
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const int es = p->d.dtype == ECC_U16 ? 2 : 1;
+    const int64_t dp_y = (g->nx * es + 15) / 16 * 16;
+    return p->ensure_stage(g->nz * g->ny * dp_y);
+}
+
+// Quantize, stencil and scan; the ECC (nbins entries) is left in the plan's
+// stage_ecc.  Only stream operations (capturable into a graph).
+cudaError_t levels_enqueue(ecc_plan_s *p, const Geom &g, const float *d_levels, int32_t m, cudaStream_t s)
+{
     const int es = p->d.dtype == ECC_U16 ? 2 : 1;
     const int64_t dp_y = (g.nx * es + 15) / 16 * 16;
     const int64_t dp_z = g.ny * dp_y;
-    st = p->ensure_stage(g.nz * dp_z);
-    if (st != ECC_OK) return st;
-
     QuantArgs a{};
     a.src = g.data;
     a.nx = g.nx;
@@ -182,7 +185,6 @@ extern "C" ecc_status ecc_compute_levels(ecc_plan_t p, const ecc_image *img, con
     cudaError_t e = es == 1 ? launch_quantize_any<unsigned char>(a, blocks, s)
                             : launch_quantize_any<unsigned short>(a, blocks, s);
     p->last_launches = 1;
-
     Geom dg = g;
     dg.data = p->stage;
     dg.esize = es;
@@ -195,6 +197,23 @@ extern "C" ecc_status ecc_compute_levels(ecc_plan_t p, const ecc_image *img, con
         e = launch_scan(p->acc, p->stage_ecc, nullptr, 1, p->nbins, p->scan_ws(), p->status, s);
         ++p->last_launches;
     }
+    return e;
+}
+
+}  // namespace ecc
+
+using namespace ecc;
+
+extern "C" ecc_status ecc_compute_levels(ecc_plan_t p, const ecc_image *img, const float *d_levels, int32_t m,
+                                         int64_t *d_ecc, void *stream)
+{
+    if (!p) return invalid("ecc_compute_levels: NULL plan");
+    if (!d_levels || !d_ecc) return invalid("ecc_compute_levels: NULL levels or output");
+    Geom g;
+    ecc_status st = levels_prepare(p, img, m, &g);
+    if (st != ECC_OK) return st;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaError_t e = levels_enqueue(p, g, d_levels, m, s);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(d_ecc, p->stage_ecc, sizeof(int64_t) * (size_t)m, cudaMemcpyDeviceToDevice, s);
     if (e != cudaSuccess) return cuda_fail(e, "ecc_compute_levels");

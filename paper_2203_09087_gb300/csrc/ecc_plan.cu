@@ -82,6 +82,7 @@ ecc_status ecc_plan_s::ensure_ring(int64_t bytes)
     }
     if ((size_t)bytes > ring_bytes) {
         if (ring) cudaFree(ring);
+    if (aux) cudaFree(aux);
         ring = nullptr;
         ring_bytes = 0;
         cudaError_t e = cudaMalloc(&ring, (size_t)bytes);
@@ -95,12 +96,37 @@ ecc_status ecc_plan_s::ensure_ring(int64_t bytes)
     return ECC_OK;
 }
 
+ecc_status ecc_plan_s::ensure_aux(int64_t bytes)
+{
+    if ((size_t)bytes > aux_bytes) {
+        if (aux) cudaFree(aux);
+        aux = nullptr;
+        aux_bytes = 0;
+        cudaError_t e = cudaMalloc(&aux, (size_t)bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            set_error("ecc_pipeline_gaussian: scratch image allocation failed");
+            return ECC_E_NOMEM;
+        }
+        aux_bytes = (size_t)bytes;
+    }
+    return ECC_OK;
+}
+
 void ecc_plan_s::release()
 {
+    if (pipe_exec) {
+        if (pipe_done) cudaEventSynchronize(pipe_done);
+        cudaGraphExecDestroy(pipe_exec);
+        pipe_exec = nullptr;
+    }
+    if (pipe_done) cudaEventDestroy(pipe_done);
+    pipe_done = nullptr;
     if (batch) release_batch(this);
     if (ws) cudaFree(ws);
     if (stage) cudaFree(stage);
     if (ring) cudaFree(ring);
+    if (aux) cudaFree(aux);
     if (stage_ecc) cudaFree(stage_ecc);
     for (int i = 0; i < kRing; ++i) {
         if (ring_copied[i]) cudaEventDestroy(ring_copied[i]);
@@ -116,6 +142,8 @@ void ecc_plan_s::release()
     stage = nullptr;
     ring = nullptr;
     ring_bytes = 0;
+    aux = nullptr;
+    aux_bytes = 0;
     stage_ecc = nullptr;
     copy_stream = nullptr;
 }

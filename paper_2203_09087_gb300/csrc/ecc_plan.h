@@ -50,6 +50,13 @@ struct ecc_plan_s {
     cudaEvent_t ring_copied[ecc::kRing] = {};
     cudaEvent_t ring_done[ecc::kRing] = {};
 
+    // float32 scratch image of the smoothing pipeline, allocated on first use
+    void *aux = nullptr;
+    size_t aux_bytes = 0;
+    // the smoothing pipeline's captured round (kept until its launches finish)
+    cudaGraphExec_t pipe_exec = nullptr;
+    cudaEvent_t pipe_done = nullptr;
+
     // tile parameter per (ndim, esize) key chosen by the autotuner
     int tuned[4] = {0, 0, 0, 0};
     // batch path: rows per 2D tile, planes per 3D tile (0 = default)
@@ -66,6 +73,7 @@ struct ecc_plan_s {
     void autotune();
     ecc_status ensure_stage(int64_t bytes);
     ecc_status ensure_ring(int64_t bytes);
+    ecc_status ensure_aux(int64_t bytes);
     int tune_param(const ecc::Geom &g) const;
     ecc::ScanWs scan_ws() const
     {
