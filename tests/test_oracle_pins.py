@@ -315,3 +315,40 @@ def test_mutants_are_caught(tmp_path, name, old, new, which):
     mutated.write_text(src[:at] + new + src[at + len(old):])
     lib_path = oracle.build(src=mutated, out=tmp_path / "libmutant.so")
     assert not _run_pins(oracle.load(lib_path)), f"mutant survived: {name}"
+
+
+# ---------------------------------------------------------------- four dimensions
+
+@pytest.mark.parametrize("mode", MODES)
+def test_random_small_4d_vs_bruteforce(mode):
+    rng = np.random.default_rng(71)
+    for _ in range(80):
+        shape = tuple(int(x) for x in rng.integers(1, 4, size=4))
+        img = rng.integers(0, 3, size=shape).astype(np.uint8)
+        assert np.array_equal(oracle.ecc(img, 0, 2, mode), pins.bruteforce_ecc(img, 0, 2, mode))
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_2x2x2x2_two_level_patterns(mode):
+    for code in range(1 << 16):
+        img = np.array([(code >> i) & 1 for i in range(16)], np.uint8).reshape(2, 2, 2, 2)
+        if code % 97 and code not in (0, 1, 0xFFFF, 0x8000):
+            continue   # every 97th of the 65536 patterns plus the extremes keeps this quick
+        assert np.array_equal(oracle.ecc(img, 0, 1, mode), pins.bruteforce_ecc(img, 0, 1, mode))
+
+
+def test_4d_closed_forms():
+    box = np.zeros((4, 5, 3, 6), np.uint8)
+    assert oracle.ecc(box, 0, 3, "vertex")[-1] == 1
+    assert list(pins.vcec_of(oracle.ecc(box + 2, 0, 3, "vertex"))) == [0, 0, 1, 0]
+    one = box.copy()
+    one[2, 2, 1, 3] = 3                         # the dark level is a box minus a vertex star: a 3-sphere
+    assert list(pins.vcec_of(oracle.ecc(one, 0, 3, "vertex"))) == [0, 0, 0, 1]
+    corner = box.copy()
+    corner[0, 0, 0, 0] = 3                      # a corner changes nothing topologically
+    assert list(pins.vcec_of(oracle.ecc(corner, 0, 3, "vertex"))) == [1, 0, 0, 0]
+    # a depth-1 4D image is the 3D volume
+    rng = np.random.default_rng(72)
+    vol = rng.integers(0, 5, size=(3, 4, 5)).astype(np.uint8)
+    for mode in MODES:
+        assert np.array_equal(oracle.ecc(vol[None], 0, 4, mode), oracle.ecc(vol, 0, 4, mode))
