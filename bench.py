@@ -406,6 +406,54 @@ def run_gaussian_pipeline(args):
                         "(sigma 2), (ECC + smoothing) x n on the device", "rounds": rows}
 
 
+def run_topcell_and_4d(args):
+    """NEXT-4 of the scope: (1) the top-cell complex (the paper's own
+    Sec. 2.1 reading) on the 512^3 benchmark volume, stencil time beside the
+    vertex complex, same flush and timing; (2) a 4D image, 64^4 uint8
+    smoothed field (sigma 2), through ecc_compute_nd."""
+    import numpy as np
+    import torch
+
+    import paper_2203_09087_gb300 as ecc
+    import synth
+    vol = synth.config2_smooth_3d(device="cuda")
+    l2 = torch.cuda.get_device_properties(torch.cuda.current_device()).L2_cache_size
+    flush = torch.empty(2 * l2 + (1 << 20), dtype=torch.uint8, device="cuda")
+    res = {}
+    for name, mode in (("vertex", ecc.ECC_VERTEX_MAX), ("topcell", ecc.ECC_TOPCELL_MIN)):
+        plan = ecc.ecc_plan("u8", 0, 255, complex_mode=mode, max_voxels=vol.numel(), flags=ecc.ECC_FLAG_TIME_KERNELS)
+        out = ecc.ecc_compute(plan, vol)
+        ecc.ecc_status_get(plan)
+        for _ in range(3):
+            flush.fill_(1)
+            ecc.ecc_compute(plan, vol, out)
+        torch.cuda.synchronize()
+        ecc.ecc_plan_kernel_time(plan)
+        for i in range(10):
+            flush.fill_(i & 0xFF)
+            ecc.ecc_compute(plan, vol, out)
+        kern_ms, kern_n = ecc.ecc_plan_kernel_time(plan)
+        res[f"{name}_512cube_stencil_us"] = kern_ms / max(kern_n, 1) * 1e3
+    g = torch.Generator(device="cuda")
+    g.manual_seed(6)
+    f = synth.smooth(torch.randn((64, 64, 64, 64), generator=g, device="cuda"), 2.0)
+    img4 = synth.quantize(f, np.uint8).contiguous()
+    plan = ecc.ecc_plan("u8", 0, 255, max_voxels=img4.numel())
+    out = ecc.ecc_compute_nd(plan, img4)
+    ecc.ecc_status_get(plan)
+    assert int(out[-1].item()) == 1
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(5):
+        ecc.ecc_compute_nd(plan, img4, out)
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / 5
+    res["4d"] = {"workload": "64^4 uint8 smoothed field (sigma 2), 256 bins, vertex complex",
+                 "ms": ms, "gvox_s": img4.numel() / (ms * 1e-3) / 1e9}
+    return res
+
+
 def run_serving(args):
     """Poisson stream of mixed 2D/3D uint8/uint16 requests (crops of resident
     seeded fields): p50/p99 latency at the nominal rate, and throughput of a
@@ -623,6 +671,7 @@ def main():
         line["single_u16"] = run_single_u16(args)
         line["float_levels"] = run_float_levels(args)
         line["gaussian_pipeline"] = run_gaussian_pipeline(args)
+        line["topcell_and_4d"] = run_topcell_and_4d(args)
         line["serving"] = run_serving(args)
     if rank == 0:
         print(json.dumps(line))

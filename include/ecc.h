@@ -87,6 +87,18 @@ typedef struct ecc_image {
     int64_t slice_pitch;
 } ecc_image;
 
+/* An image of 2 to 4 dimensions (ecc_compute_nd).  dims[0..ndim-1] >= 1,
+ * dims[0] slowest.  pitches[a] (a = 0 .. ndim-2): bytes between
+ * consecutive indices of axis a; 0 = dense.  Pitches must be multiples of
+ * the element size and hold the extent of the axes inside them. */
+typedef struct ecc_image_nd {
+    const void *data;
+    int32_t ndim;
+    int32_t dtype;          /* ECC_U8 or ECC_U16 */
+    int64_t dims[4];
+    int64_t pitches[3];
+} ecc_image_nd;
+
 /* Plan flags. */
 #define ECC_FLAG_NO_RANGE_CHECK   0x1u  /* caller guarantees lo <= value <= hi */
 #define ECC_FLAG_NO_AUTOTUNE      0x2u  /* use built-in tile defaults, never time candidates */
@@ -186,6 +198,17 @@ ecc_status ecc_compute_levels(ecc_plan_t plan, const ecc_image *img, const float
 ecc_status ecc_pipeline_gaussian(ecc_plan_t plan, const ecc_image *img, const float *h_taps, int32_t ntaps,
                                  int32_t iterations, const float *d_levels, int32_t m, int64_t *d_ecc,
                                  void *stream);
+
+/* ECC of a 2D, 3D or 4D device image (d > 3: the paper's method in any
+ * dimension, Sec. 2.1-2.3; its texture-based kernel stops at three, Sec. 5).
+ * 2D and 3D images go to ecc_compute.  A 4D image takes a one-thread-per-
+ * voxel kernel: 80 neighbour comparisons (ties to the lower linear index)
+ * and the signed count of the 81 cells containing the voxel (1 vertex, 8
+ * edges, 24 squares, 32 cubes, 16 tesseracts), both complexes, the same
+ * histogram and scan.  Arguments and errors as ecc_compute; the image's
+ * voxel count must not exceed max_voxels. */
+ecc_status ecc_compute_nd(ecc_plan_t plan, const ecc_image_nd *img, int64_t *d_ecc, int64_t *d_vcec,
+                          void *stream);
 
 /* Out-of-core ECC of a HOST image of any size (Sec. 3.4, Fig. 5: the
  * streaming that lets the paper process volumes larger than device memory).

@@ -11,6 +11,7 @@ memory and streams only.  The functions keep the C names:
     ecc_big = ecc_compute_stream(plan, huge_array, 1 << 30)  # ecc_compute_stream (out of core)
     ecc_t = ecc_compute_levels(plan_u16, f32_tensor, levels)  # ecc_compute_levels (float thresholds)
     eccs = ecc_pipeline_gaussian(plan_u16, f32_tensor, gaussian_taps(2.0), 100, levels)  # Table 2 loop
+    ecc4 = ecc_compute_nd(plan, tensor_4d)               # ecc_compute_nd (2D, 3D or 4D)
     srv = ecc_server_create(budget_bytes, n_streams=4)  # ecc_server_create / ecc_submit / ...
 
 There is no CPU fallback: importing works anywhere, but the first call loads
@@ -47,6 +48,7 @@ from ._binding import (  # noqa: F401
     ecc_compute_batch,
     ecc_compute_host,
     ecc_compute_levels,
+    ecc_compute_nd,
     ecc_pipeline_gaussian,
     gaussian_taps,
     ecc_compute_stream,

@@ -38,6 +38,11 @@ class EccImage(ctypes.Structure):
                 ("dims", ctypes.c_int64 * 3), ("row_pitch", ctypes.c_int64), ("slice_pitch", ctypes.c_int64)]
 
 
+class EccImageNd(ctypes.Structure):
+    _fields_ = [("data", ctypes.c_void_p), ("ndim", ctypes.c_int32), ("dtype", ctypes.c_int32),
+                ("dims", ctypes.c_int64 * 4), ("pitches", ctypes.c_int64 * 3)]
+
+
 class EccPlanDesc(ctypes.Structure):
     _fields_ = [("dtype", ctypes.c_int32), ("lo", ctypes.c_int32), ("hi", ctypes.c_int32),
                 ("complex_mode", ctypes.c_int32), ("max_images", ctypes.c_int32), ("reserved", ctypes.c_int32),
@@ -62,6 +67,7 @@ _SIGNATURES = {
     "ecc_compute_batch": (ctypes.c_int, [_VP, _I32, ctypes.POINTER(EccImage), _VP, _VP]),
     "ecc_compute_stream": (ctypes.c_int, [_VP, ctypes.POINTER(EccImage), _VP, _I64, _VP]),
     "ecc_compute_levels": (ctypes.c_int, [_VP, ctypes.POINTER(EccImage), _VP, _I32, _VP, _VP]),
+    "ecc_compute_nd": (ctypes.c_int, [_VP, ctypes.POINTER(EccImageNd), _VP, _VP, _VP]),
     "ecc_pipeline_gaussian": (ctypes.c_int, [_VP, ctypes.POINTER(EccImage), _VP, _I32, _I32, _VP, _I32, _VP, _VP]),
     "ecc_compute_noalloc": (ctypes.c_int, [ctypes.POINTER(EccImage), _I32, _I32, _I32, ctypes.c_uint32, _VP, _VP,
                                            _VP]),
@@ -277,6 +283,33 @@ def ecc_compute_levels(plan: Plan, image, levels, out=None, stream=None):
     _check_out(out, m)
     _check(library().ecc_compute_levels(plan.handle, ctypes.byref(d), levels.data_ptr(), m, out.data_ptr(),
                                         _stream_handle(stream)))
+    return out
+
+
+def ecc_compute_nd(plan: Plan, image, out=None, vcec_out=None, stream=None):
+    """ECC of a 2D, 3D or 4D uint8/uint16 CUDA tensor; returns the int64 CUDA tensor ``out``."""
+    import torch
+    if not isinstance(image, torch.Tensor) or not image.is_cuda:
+        raise ValueError("the image must be a CUDA tensor")
+    if image.dim() not in (2, 3, 4) or image.stride(-1) != 1:
+        raise ValueError("the image must be 2D, 3D or 4D with a contiguous innermost axis")
+    d = EccImageNd()
+    d.data = image.data_ptr()
+    d.ndim = image.dim()
+    d.dtype = _dtype_code(image.dtype)
+    es = image.element_size()
+    for i, n in enumerate(image.shape):
+        d.dims[i] = int(n)
+    for i in range(image.dim() - 1):
+        d.pitches[i] = int(image.stride(i)) * es
+    if out is None:
+        out = torch.empty(plan.nbins, dtype=torch.int64, device=image.device)
+    _check_out(out, plan.nbins)
+    vptr = None
+    if vcec_out is not None:
+        _check_out(vcec_out, plan.nbins)
+        vptr = vcec_out.data_ptr()
+    _check(library().ecc_compute_nd(plan.handle, ctypes.byref(d), out.data_ptr(), vptr, _stream_handle(stream)))
     return out
 
 
