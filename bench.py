@@ -406,6 +406,41 @@ def run_gaussian_pipeline(args):
                         "(sigma 2), (ECC + smoothing) x n on the device", "rounds": rows}
 
 
+def run_config1_latency(args):
+    """C1, the 256x256 uint8 uniform image: too small to fill the GPU, so the
+    figure is the latency of one ecc_compute call (stencil + scan) measured
+    with CUDA events on the stream, median of 200 calls, and the same for a
+    call through ecc_compute_host (host image in, host ECC out)."""
+    import numpy as np
+    import torch
+
+    import paper_2203_09087_gb300 as ecc
+    import synth
+    img = synth.config1_uniform_2d()
+    t = torch.from_numpy(img).cuda()
+    plan = ecc.ecc_plan("u8", 0, 255, max_voxels=t.numel())
+    out = ecc.ecc_compute(plan, t)
+    ecc.ecc_status_get(plan)
+    ts = []
+    for _ in range(200):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        ecc.ecc_compute(plan, t, out)
+        b.record()
+        b.synchronize()
+        ts.append(a.elapsed_time(b) * 1e3)
+    host = np.ascontiguousarray(img)
+    hout = np.empty(256, np.int64)
+    hs = []
+    for _ in range(50):
+        t0 = time.perf_counter()
+        ecc.ecc_compute_host(plan, host, hout)
+        hs.append((time.perf_counter() - t0) * 1e6)
+    assert np.array_equal(hout, out.cpu().numpy())
+    return {"workload": "256x256 uint8 uniform [0,255], seed 0, 256 bins", "device_call_us_p50": float(np.median(ts)),
+            "device_call_us_p99": float(np.percentile(ts, 99)), "host_call_us_p50": float(np.median(hs))}
+
+
 def run_topcell_and_4d(args):
     """NEXT-4 of the scope: (1) the top-cell complex (the paper's own
     Sec. 2.1 reading) on the 512^3 benchmark volume, stencil time beside the
@@ -672,6 +707,7 @@ def main():
         line["float_levels"] = run_float_levels(args)
         line["gaussian_pipeline"] = run_gaussian_pipeline(args)
         line["topcell_and_4d"] = run_topcell_and_4d(args)
+        line["config1"] = run_config1_latency(args)
         line["serving"] = run_serving(args)
     if rank == 0:
         print(json.dumps(line))
