@@ -104,3 +104,15 @@ def test_stream_full_size_512cube_against_device_path():
     got = ecc.ecc_compute_stream(plan, host, 64 << 20)
     assert np.array_equal(got, want)
     assert got[-1] == 1
+
+
+def test_host_path_many_chunks_against_device_path():
+    """ecc_compute_host with more chunks than the plan's chunk events (157 MB
+    in 8 MiB chunks) equals the device-resident ECC."""
+    import synth
+    ecc = ecc_mod()
+    vol = synth.config2_smooth_3d(device="cuda", shape=(600, 512, 512))
+    plan = ecc.ecc_plan("u8", 0, 255, max_voxels=vol.numel())
+    want = ecc.ecc_compute(plan, vol).cpu().numpy()
+    host = vol.cpu().pin_memory().numpy()
+    assert np.array_equal(ecc.ecc_compute_host(plan, host), want)
