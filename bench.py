@@ -441,6 +441,45 @@ def run_config1_latency(args):
             "device_call_us_p99": float(np.percentile(ts, 99)), "host_call_us_p50": float(np.median(hs))}
 
 
+def run_cpu_baselines(args):
+    """The CPU oracle (as it stands, one host thread) on the other
+    configurations, each a bounded sample: C1 in full, a slab of planes of
+    the C3 volume (65536 bins), and the first 2D images and first 3D patches
+    of the C4 batch.  Reported baselines, not targets."""
+    import numpy as np
+
+    import oracle
+    import synth
+    res = {}
+    img = synth.config1_uniform_2d()
+    t0 = time.perf_counter()
+    oracle.ecc(img, 0, 255, oracle.VERTEX)
+    dt = time.perf_counter() - t0
+    res["config1"] = {"value": img.size / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+                      "sample": "the whole 256x256 image"}
+    vol = synth.config3_smooth_blobs_u16(device="cuda").cpu().numpy()
+    t0 = time.perf_counter()
+    planes = 6
+    oracle.vcec_rows(vol, 0, planes, 0, 65535, oracle.VERTEX)
+    dt = time.perf_counter() - t0
+    res["config3"] = {"value": planes * vol.shape[1] * vol.shape[2] / dt / 1e9, "unit": UNIT, "cores": 1,
+                      "kind": "oracle", "sample": f"cells based on planes 0..{planes - 1} of the 1024^3 uint16 volume"}
+    del vol
+    specs = synth.batch_specs()
+    pick = [i for i, (shape, _) in enumerate(specs) if len(shape) == 2][:16] + \
+           [i for i, (shape, _) in enumerate(specs) if len(shape) == 3][:2]
+    imgs = [synth.smoothed_field(specs[i][0], specs[i][1], np.uint8, seed=3 * 100003 + i, device="cuda").cpu().numpy()
+            for i in pick]
+    t0 = time.perf_counter()
+    for im in imgs:
+        oracle.ecc(im, 0, 255, oracle.VERTEX)
+    dt = time.perf_counter() - t0
+    vox = sum(im.size for im in imgs)
+    res["config4"] = {"value": vox / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+                      "sample": f"the first 16 2D images and first 2 3D patches of the batch ({vox} voxels)"}
+    return res
+
+
 def run_topcell_and_4d(args):
     """NEXT-4 of the scope: (1) the top-cell complex (the paper's own
     Sec. 2.1 reading) on the 512^3 benchmark volume, stencil time beside the
@@ -708,6 +747,8 @@ def main():
         line["gaussian_pipeline"] = run_gaussian_pipeline(args)
         line["topcell_and_4d"] = run_topcell_and_4d(args)
         line["config1"] = run_config1_latency(args)
+        if not args.no_cpu:
+            line["cpu_baselines_1core"] = run_cpu_baselines(args)
         line["serving"] = run_serving(args)
     if rank == 0:
         print(json.dumps(line))
