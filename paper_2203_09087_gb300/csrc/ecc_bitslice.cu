@@ -14,16 +14,18 @@
 //    register: no halo bits have to be fetched from neighbouring windows.
 //  * Lanes along y, CTA walks z.  Lane l of a warp holds row y0-1+l (lanes 0
 //    and 31 are the y halo); the CTA walks planes z upward.  Each of the 13
-//    neighbour directions is compared once per voxel pair: a lane compares
-//    its rows (z,y), (z,y+1) against (z+1,y), (z+1,y+1) and the in-plane
-//    pairs, and receives the pairs it shares with row y-1 by warp shuffles.
-//    A voxel's wins over earlier neighbours are the negations of those
-//    neighbours' comparisons (ties go to the lower linear index).
+//    neighbour directions is compared once per voxel pair (ecc_walk.cuh):
+//    plane z against plane z+1 and the in-plane pairs of z+1, the pairs
+//    with rows y-1 and y+1 exchanged by warp shuffles.  A voxel's wins over
+//    earlier neighbours are the negations of those neighbours' comparisons
+//    (ties go to the lower linear index).  The cell count groups the 26
+//    signed cell terms into 12 one-bit chains (ecc_bitslice.cuh).
 //  * TMA ring.  One elected thread streams one tile plane per step
 //    (cp.async.bulk.tensor, mbarrier completion) into a ring of stages; the
 //    box starts 16-byte aligned and is an odd number of 16-byte units wide so
 //    the per-lane 16-byte shared loads are bank-conflict free.  The
-//    boundary is handled by existence masks, never by the zero fill.
+//    boundary is an extra bit plane set from coordinates (a missing voxel
+//    compares as 2^K), never the zero fill.
 //  * Histogram.  Only voxels whose signed cell count is nonzero (rare in
 //    smooth fields) are emitted, into replicated shared-memory int32
 //    histograms flushed once per CTA into the int64 accumulator, or
