@@ -170,3 +170,23 @@ def test_destroy_with_cancel_drains_or_cancels():
     srv.close(cancel=True)
     # nothing hangs; the handle is gone
     assert not srv.handle.value
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_batch_degenerate_and_boundary_shapes(mode):
+    """Shapes at the edges of the 2D lane packing (one window of 30 columns,
+    one row, row counts around the row-chunk length) and of the 3D tiles."""
+    ecc = ecc_mod()
+    rng = np.random.default_rng(17 + mode)
+    shapes = [(1, 1), (1, 70), (70, 1), (3, 31), (31, 3), (29, 30), (30, 31), (33, 61), (64, 64),
+              (5, 960), (2, 961), (15, 17), (16, 900), (31, 29), (32, 33), (63, 30), (65, 91), (97, 2),
+              (1, 1, 1), (1, 31, 1), (2, 2, 33), (31, 33, 1), (17, 30, 31), (9, 61, 29)]
+    imgs = [rng.integers(0, int(rng.choice([2, 7, 256])), size=s).astype(np.uint8) for s in shapes]
+    plan = ecc.ecc_plan("u8", 0, 255, complex_mode=mode, max_images=len(imgs),
+                        max_voxels=sum(i.size for i in imgs))
+    got = ecc.ecc_compute_batch(plan, [torch.from_numpy(i).cuda() for i in imgs])
+    ecc.ecc_status_get(plan)
+    got = got.cpu().numpy()
+    om = oracle.VERTEX if mode == 0 else oracle.TOPCELL
+    for k, img in enumerate(imgs):
+        assert np.array_equal(got[k], oracle.ecc(img, 0, 255, om)), (k, img.shape)
