@@ -108,14 +108,21 @@ __global__ void __launch_bounds__(kNdThreads) direct4d_kernel(const Nd4Args a)
                              (win[2] & kCellMask[cell][2]) == kCellMask[cell][2];
             kappa += won ? kCellSign[cell] : 0;
         }
-        if (kappa) {
+        {
             const int bin = v - a.h.lo;
-            if (a.range_check && (unsigned)bin >= (unsigned)a.h.nbins) {
-                atomicOr(a.status, DEV_RANGE);
-            } else if (a.smem_hist) {
-                atomicAdd(&hist4[bin], kappa);
-            } else {
-                atomicAdd(a.h.acc + bin, (unsigned long long)(long long)kappa);
+            const bool bad = kappa && a.range_check && (unsigned)bin >= (unsigned)a.h.nbins;
+            if (bad) atomicOr(a.status, DEV_RANGE);
+            const bool add = kappa && !bad;
+            // lanes adding to the same bin combine first (neighbouring voxels of
+            // a smooth field often share a gray level)
+            const unsigned act = __activemask();
+            const unsigned grp = __match_any_sync(act, add ? bin : -1 - (int)(threadIdx.x & 31));
+            const int sum = __reduce_add_sync(grp, kappa);
+            if (add && (int)(threadIdx.x & 31) == __ffs(grp) - 1 && sum) {
+                if (a.smem_hist)
+                    atomicAdd(&hist4[bin], sum);
+                else
+                    atomicAdd(a.h.acc + bin, (unsigned long long)(long long)sum);
             }
         }
     }
