@@ -117,6 +117,13 @@ static cudaError_t launch_stencil_untimed(ecc_plan_s *p, const Geom &g, int64_t 
             return e;
         }
     }
+    // a whole 3D image whose rows the TMA cannot address (pitch not a multiple
+    // of 16 bytes): the persistent batch kernel walks it with global loads
+    if (want_bitslice && g.ndim == 3 && ob == 0 && oe == g.nz && !h.emitted) {
+        cudaError_t e = launch_batch_single(p, g, h, s);
+        p->last_launches += 2;
+        return e;
+    }
     ++p->last_launches;
     return launch_direct(g, ob, oe, h, p->d.complex_mode, range, p->status, p->num_sms, s);
 }
@@ -277,15 +284,16 @@ ecc_status ecc_compute_host(ecc_plan_t p, const ecc_image *h_img, int64_t *h_ecc
     ecc_status st = image_geom(h_img, p->d.dtype, p->d.max_voxels, &hg, &nvox, false);
     if (st != ECC_OK) return st;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    st = p->ensure_stage(nvox * hg.esize);
+    st = p->ensure_stage((hg.ndim == 3 ? hg.nz : 1) * hg.ny * ((hg.nx * hg.esize + 15) / 16 * 16));
     if (st != ECC_OK) return st;
 
     // Dense device copy of the image, filled chunk by chunk along the outer
     // axis (Sec. 3.4): chunk k is processed once chunk k+1 -- which holds
     // its one-voxel collar -- has arrived, so copies overlap the kernels.
+    // rows padded to 16 bytes: every chunk takes the TMA kernel
     Geom dg = hg;
     dg.data = p->stage;
-    dg.pitch_y = hg.nx * hg.esize;
+    dg.pitch_y = (hg.nx * hg.esize + 15) / 16 * 16;
     dg.pitch_z = hg.ny * dg.pitch_y;
     const int64_t outer = hg.ndim == 3 ? hg.nz : hg.ny;
     const int64_t outer_bytes = hg.ndim == 3 ? dg.pitch_z : dg.pitch_y;
@@ -307,10 +315,9 @@ ecc_status ecc_compute_host(ecc_plan_t p, const ecc_image *h_img, int64_t *h_ecc
         unsigned char *dst = p->stage + a * outer_bytes;
         const unsigned char *src = static_cast<const unsigned char *>(h_img->data);
         if (hg.ndim == 3) {
-            const bool dense = hg.pitch_y == dg.pitch_y && hg.pitch_z == dg.pitch_z;
-            if (dense) {
-                e = cudaMemcpyAsync(dst, src + a * hg.pitch_z, (b - a) * outer_bytes, cudaMemcpyHostToDevice,
-                                    p->copy_stream);
+            if (hg.pitch_z == hg.ny * hg.pitch_y) {   // host slices contiguous: one 2D copy of all rows
+                e = cudaMemcpy2DAsync(dst, dg.pitch_y, src + a * hg.pitch_z, hg.pitch_y, hg.nx * hg.esize,
+                                      (b - a) * hg.ny, cudaMemcpyHostToDevice, p->copy_stream);
             } else {
                 for (int64_t z = a; z < b && e == cudaSuccess; ++z)
                     e = cudaMemcpy2DAsync(p->stage + z * dg.pitch_z, dg.pitch_y, src + z * hg.pitch_z, hg.pitch_y,

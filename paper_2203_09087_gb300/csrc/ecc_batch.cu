@@ -63,6 +63,10 @@ struct BatchState {
     unsigned scan_grid = 0;
     int persistent_ctas = 0;
     int chunk2d = 32, chunk3d = 16;
+    // the persistent kernel and its shared memory, for single-image launches
+    void *fn = nullptr;
+    size_t smem = 0;
+    bool smem_hist = false;
 };
 
 namespace {
@@ -335,6 +339,9 @@ cudaError_t capture_graph(ecc_plan_s *p, BatchState *b)
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorNotSupported;
     b->persistent_ctas = p->num_sms * per_sm;
+    b->fn = fn;
+    b->smem = smem;
+    b->smem_hist = smem_hist;
 
     BatchArgs args{};  // the kernel nodes copy their arguments at creation
     args.hdr = reinterpret_cast<const BatchHeader *>(b->d_desc);
@@ -424,6 +431,53 @@ ecc_status ensure_batch(ecc_plan_s *p)
 }
 
 }  // namespace
+
+namespace {
+
+// The work list of one image, written on the device from a by-value
+// descriptor (no host staging, so a single-image call never waits).
+__global__ void init_single(BatchArgs a, BatchImage im)
+{
+    BatchHeader *hdr = const_cast<BatchHeader *>(a.hdr);
+    hdr->n = 1;
+    const_cast<BatchImage *>(a.img)[0] = im;
+    a.start[0] = 0;
+    a.start[1] = tiles_of(im, a.chunk2d, a.chunk3d);
+    *a.counter = 0u;
+}
+
+}  // namespace
+
+// One whole 3D image through the persistent batch kernel (any pitch: rows
+// come from aligned 32-bit global loads): the path for images whose row
+// pitch rules out the TMA kernel.  Two stream launches (work list, kernel);
+// accumulates into h.acc like the other stencils.
+cudaError_t launch_batch_single(ecc_plan_s *p, const Geom &g, const HistDst &h, cudaStream_t s)
+{
+    if (ensure_batch(p) != ECC_OK) return cudaErrorMemoryAllocation;
+    BatchState *b = p->batch;
+    BatchArgs args{};
+    args.hdr = reinterpret_cast<const BatchHeader *>(b->d_desc);
+    args.img = reinterpret_cast<const BatchImage *>(b->d_desc + sizeof(BatchHeader));
+    args.start = b->d_start;
+    args.counter = b->d_counter;
+    args.acc = h.acc;
+    args.lo = h.lo;
+    args.nbins = h.nbins;
+    args.chunk2d = b->chunk2d;
+    args.chunk3d = b->chunk3d;
+    args.smem_hist = b->smem_hist;
+    args.range_check = !(p->d.flags & ECC_FLAG_NO_RANGE_CHECK);
+    args.status = p->status;
+    const BatchImage im{g.data, g.nx, g.ny, g.nz, g.pitch_y, g.pitch_z, g.ndim, g.esize};
+    init_single<<<1, 1, 0, s>>>(args, im);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) {
+        void *argv[] = {&args};
+        e = cudaLaunchKernel(b->fn, dim3((unsigned)b->persistent_ctas), dim3(kBatchWarps * 32), argv, b->smem, s);
+    }
+    return e;
+}
 
 void release_batch(ecc_plan_s *p)
 {
