@@ -91,12 +91,11 @@ __global__ void __launch_bounds__(256) store_row(const long long *stage, int64_t
 }
 
 cudaError_t blur_pass(const float *in, int64_t in_sy, int64_t in_sz, float *out, int64_t out_sy, int64_t out_sz,
-                      const Geom &g, int axis, const Taps &t, int num_sms, cudaStream_t s)
+                      const Geom &g, int axis, const Taps &t, cudaStream_t s)
 {
     BlurArgs a{in, out, g.nx, g.ny, g.nz, in_sy, in_sz, out_sy, out_sz, axis};
     const int64_t bx = std::min<int64_t>((g.nx + kBlurThreads - 1) / kBlurThreads, 64);
     const int64_t by = std::min<int64_t>(g.ny * g.nz, 65535);
-    (void)num_sms;
     blur_kernel<<<dim3((unsigned)bx, (unsigned)by), kBlurThreads, 0, s>>>(a, t);
     return cudaGetLastError();
 }
@@ -149,9 +148,9 @@ extern "C" ecc_status ecc_pipeline_gaussian(ecc_plan_t p, const ecc_image *img, 
         // passes alternate image -> tmp -> image ...; an odd count ends with a copy back
         for (int ax = 0; ax < axes && e == cudaSuccess; ++ax) {
             if (ax % 2 == 0)
-                e = blur_pass(im, im_sy, im_sz, tmp, t_sy, t_sz, g, ax, t, p->num_sms, cs);
+                e = blur_pass(im, im_sy, im_sz, tmp, t_sy, t_sz, g, ax, t, cs);
             else
-                e = blur_pass(tmp, t_sy, t_sz, im, im_sy, im_sz, g, ax, t, p->num_sms, cs);
+                e = blur_pass(tmp, t_sy, t_sz, im, im_sy, im_sz, g, ax, t, cs);
         }
         if (e == cudaSuccess && axes % 2 == 1) {
             if (g.pitch_z == g.ny * g.pitch_y)   // slices contiguous: one copy of all rows
