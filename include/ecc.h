@@ -201,12 +201,12 @@ ecc_status ecc_pipeline_gaussian(ecc_plan_t plan, const ecc_image *img, const fl
 
 /* ECC of a 2D, 3D or 4D device image (d > 3: the paper's method in any
  * dimension, Sec. 2.1-2.3; its texture-based kernel stops at three, Sec. 5).
- * 2D and 3D images go to ecc_compute.  A 4D image takes a one-thread-per-
- * voxel kernel: 80 neighbour comparisons (ties to the lower linear index)
- * and the signed count of the 81 cells containing the voxel (1 vertex, 8
- * edges, 24 squares, 32 cubes, 16 tesseracts), both complexes, the same
- * histogram and scan.  Arguments and errors as ecc_compute; the image's
- * voxel count must not exceed max_voxels. */
+ * 2D and 3D images go to ecc_compute.  A 4D image takes a bit-sliced
+ * walker: the wins over the 80 neighbours (ties to the lower linear index)
+ * give the signed count of the 81 cells containing the voxel (1 vertex, 8
+ * edges, 24 squares, 32 cubes, 16 tesseracts) as three 3D counts, both
+ * complexes, the same histogram and scan.  Arguments and errors as ecc_compute; the image's voxel count must not
+ * exceed max_voxels. */
 ecc_status ecc_compute_nd(ecc_plan_t plan, const ecc_image_nd *img, int64_t *d_ecc, int64_t *d_vcec,
                           void *stream);
 

@@ -214,6 +214,81 @@ BS_HD uint32_t kappa3d(const uint32_t w[3][3][3], uint32_t T[4])
     return ~T[0] | T[1] | ~T[2] | T[3];
 }
 
+// ---------------------------------------------------------------- 4D cells
+//
+// Wins over the 80 neighbours as masks w[dw+1][dz+1][dy+1][dx+1] (centre
+// unused).  The star of the voxel splits along w: the cells of its own
+// hyperplane (count kappa3d of the in-hyperplane wins W0), and each such cell
+// extended to w+1 (or w-1), one dimension higher, which the voxel wins when
+// it beats its w-neighbour (b+) and the cell's vertices in both hyperplanes
+// (W0 & W+).  Hence
+//   kappa4 = k3(W0) - b+ k3(W0 & W+) - b- k3(W0 & W-),   k3 = T - 5,
+// and kappa4 != 0 iff X != Y with X = T0 + 5 (b+ + b-) and
+// Y = b+ T+ + b- T- + 5 (both at most 32, six bit planes).
+
+// x + y over n-bit planes (carry out dropped: callers keep sums in range).
+template <int N>
+BS_HD void add_planes(const uint32_t *x, const uint32_t *y, uint32_t *out)
+{
+    uint32_t c = 0;
+#pragma unroll
+    for (int k = 0; k < N; ++k) {
+        const uint32_t a = x[k], b = y[k];
+        out[k] = a ^ b ^ c;
+        c = (a & b) | (a & c) | (b & c);
+    }
+}
+
+// Nonzero mask of kappa4 from the chain counts T0 = T(W0), Tp = T(W0 & W+),
+// Tm = T(W0 & W-) (four planes each) and the w-wins bp = b+, bm = b-.
+BS_HD uint32_t kappa4_nonzero(const uint32_t *T0, const uint32_t *Tp, const uint32_t *Tm, uint32_t bp, uint32_t bm)
+{
+    // X = T0 + 5 (bp + bm); 5 (bp + bm) is 0, 5 or 10: planes (one, both, one, both)
+    const uint32_t both = bp & bm, one = bp ^ bm;
+    const uint32_t f[6] = {one, both, one, both, 0u, 0u};
+    const uint32_t t0[6] = {T0[0], T0[1], T0[2], T0[3], 0u, 0u};
+    uint32_t X[6];
+    add_planes<6>(t0, f, X);
+    // Y = (bp & Tp) + (bm & Tm) + 5
+    const uint32_t p[6] = {bp & Tp[0], bp & Tp[1], bp & Tp[2], bp & Tp[3], 0u, 0u};
+    const uint32_t q[6] = {bm & Tm[0], bm & Tm[1], bm & Tm[2], bm & Tm[3], 0u, 0u};
+    uint32_t pq[6], Y[6];
+    add_planes<6>(p, q, pq);
+    const uint32_t five[6] = {~0u, 0u, ~0u, 0u, 0u, 0u};
+    add_planes<6>(pq, five, Y);
+    uint32_t nz = 0;
+#pragma unroll
+    for (int k = 0; k < 6; ++k) nz |= X[k] ^ Y[k];
+    return nz;
+}
+
+// All 80 wins at once (w[1][1][1][1] unused).  Returns the nonzero mask and
+// the planes kappa4_at needs.
+BS_HD uint32_t kappa4d(const uint32_t w[3][3][3][3], uint32_t T0[4], uint32_t Tp[4], uint32_t Tm[4], uint32_t &bp,
+                       uint32_t &bm)
+{
+    uint32_t a[3][3][3];
+#pragma unroll
+    for (int i = 0; i < 27; ++i) (&a[0][0][0])[i] = (&w[1][0][0][0])[i];
+    kappa3d(a, T0);
+#pragma unroll
+    for (int i = 0; i < 27; ++i) (&a[0][0][0])[i] = (&w[1][0][0][0])[i] & (&w[2][0][0][0])[i];
+    kappa3d(a, Tp);
+#pragma unroll
+    for (int i = 0; i < 27; ++i) (&a[0][0][0])[i] = (&w[1][0][0][0])[i] & (&w[0][0][0][0])[i];
+    kappa3d(a, Tm);
+    bp = w[2][1][1][1];
+    bm = w[0][1][1][1];
+    return kappa4_nonzero(T0, Tp, Tm, bp, bm);
+}
+
+// kappa4 of the voxel at bit i from kappa4d's planes.
+BS_HD int kappa4_at(const uint32_t *T0, const uint32_t *Tp, const uint32_t *Tm, uint32_t bp, uint32_t bm, int i)
+{
+    const int k0 = bits_at<4>(T0, i) - 5, kp = bits_at<4>(Tp, i) - 5, km = bits_at<4>(Tm, i) - 5;
+    return k0 - (int)((bp >> i) & 1u) * kp - (int)((bm >> i) & 1u) * km;
+}
+
 // 2D: w[dy+1][dx+1]; kappa = 1 - F + Q with F faces (of 4) and Q squares
 // (of 4).  Each face pairs with a square containing it: (1 - f) + q with
 // q => f is the bit ~f | q, so kappa = X[0] + X[1] + 2 X[2] - 3 where

@@ -1,6 +1,6 @@
 // ecc_nd.cu -- images of up to four dimensions (d > 3: the paper's texture
 // path stops at three, Sec. 5).  ecc_compute_nd forwards 2D and 3D images to
-// ecc_compute; 4D images take a one-thread-per-voxel kernel.
+// ecc_compute; 4D images take the bit-sliced walker below.
 //
 // The per-voxel rule is the one of every other kernel here (Sec. 2.3,
 // Algorithm 1 regrouped per voxel): a voxel p introduces a cell containing
@@ -8,182 +8,186 @@
 // such cell to the bin of its value.  In four dimensions the cells
 // containing p are p + sum over a in A of {0, s_a e_a} for an axis subset A
 // and signs s_A: 1 vertex, 8 edges, 24 squares, 32 cubes and 16 tesseracts.
-// The kernel compares p with its 80 neighbours (ties go to the lower linear
-// index: a neighbour later in memory is beaten on >=, an earlier one on >),
-// keeps the wins as an 81-bit mask, and counts the 81 cells against
-// precomputed masks of the neighbours each cell needs.  Vertex complex: a
-// missing neighbour is never beaten (the cell does not exist).  Top-cell
-// complex: comparisons reversed, a missing neighbour always beaten (the
-// +infinity collar), and the count multiplied by (-1)^4 = +1.
+// Ties go to the lower linear index (a neighbour later in memory is beaten
+// on >=, an earlier one on >).  Vertex complex: a missing neighbour is never
+// beaten (the cell does not exist).  Top-cell complex: comparisons reversed,
+// a missing neighbour always beaten (the +infinity collar), and the count
+// multiplied by (-1)^4 = +1.
 #include <cuda_runtime.h>
 
 #include <algorithm>
-#include <mutex>
 
+#include "ecc_bitslice.cuh"
 #include "ecc_internal.h"
 #include "ecc_plan.h"
+#include "ecc_walk.cuh"
 
 namespace ecc {
 namespace {
 
-constexpr int kNdThreads = 256;
-constexpr int kCells4 = 81;
+// ------------------------------------------------------------ bit-sliced walker
+//
+// The star of a voxel splits along w into the cells of its own hyperplane
+// and those cells extended to w+1 or w-1, so its count is
+//   kappa4 = k3(W0) - b+ k3(W0 & W+) - b- k3(W0 & W-)
+// with W0, W+, W- its wins over hyperplanes w, w+1, w-1, b+- its wins over
+// its two w-neighbours and k3 the 3D count (bs::kappa4_nonzero).  Each warp
+// takes one (z, 30-row tile, 30-column window) column over a chunk of w: it
+// holds slices (w, z-1..z+1), loads (w+1, z-1..z+1) at every step, and
+// compares slices in blocks of nine directions (walk::slice_pair), each
+// pair of voxels at most once per warp.  The wins over hyperplane w-1 are
+// the complements carried from the step before.
+constexpr int kWalk4Warps = 4;
 
-// Cell c needs the neighbours in bits of kCellMask[c][0..2] (neighbour index
-// (dw+1)*27 + (dz+1)*9 + (dy+1)*3 + (dx+1); 40 is the voxel itself) and
-// counts kCellSign[c] = (-1)^dim.
-__constant__ uint32_t kCellMask[kCells4][3];
-__constant__ int kCellSign[kCells4];
-
-struct Nd4Args {
+struct Walk4Args {
     const unsigned char *data;
-    int64_t n[4];        // dims, slowest first: w, z, y, x
+    int64_t n[4];        // w, z, y, x
     int64_t pitch[3];    // bytes: w, z, y
+    int64_t items;       // w chunks x nz x row tiles x windows
+    int32_t ntx, nty;    // windows of 30 columns, tiles of 30 rows
+    int64_t chunk;       // hyperplanes per item
     HistDst h;
     int32_t smem_hist, range_check;
     unsigned int *status;
 };
 
 template <typename T, bool TOP>
-__global__ void __launch_bounds__(kNdThreads) direct4d_kernel(const Nd4Args a)
+__global__ void __launch_bounds__(kWalk4Warps * 32) walk4d_kernel(const Walk4Args a)
 {
-    extern __shared__ int hist4[];
+    constexpr int K = 8 * sizeof(T), KP = K + 1;
+    extern __shared__ int hist4w[];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (a.smem_hist)
-        for (int i = threadIdx.x; i < a.h.nbins; i += blockDim.x) hist4[i] = 0;
+        for (int i = threadIdx.x; i < a.h.nbins; i += blockDim.x) hist4w[i] = 0;
     __syncthreads();
-    const int64_t total = a.n[0] * a.n[1] * a.n[2] * a.n[3];
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
-         i += (int64_t)gridDim.x * blockDim.x) {
-        int64_t c[4];
-        int64_t r = i;
-        for (int ax = 3; ax >= 0; --ax) {
-            c[ax] = r % a.n[ax];
-            r /= a.n[ax];
-        }
-        const unsigned char *pp = a.data + c[0] * a.pitch[0] + c[1] * a.pitch[1] + c[2] * a.pitch[2] + c[3] * sizeof(T);
-        const int v = (int)*reinterpret_cast<const T *>(pp);
-        // neighbour (dw, dz, dy, dx) has index k = (dw+1)*27 + (dz+1)*9 + (dy+1)*3 + (dx+1);
-        // addresses and "inside the image" flags are built axis by axis
-        bool lo_ok[4], hi_ok[4];
+    const walk::Bins bins{a.smem_hist ? hist4w : nullptr, a.h.acc, a.h.lo, a.h.nbins, a.range_check, a.status};
+    const int64_t nw = a.n[0], nz = a.n[1], ny = a.n[2], nx = a.n[3];
+    const int64_t row_bytes = nx * (int64_t)sizeof(T);
+    unsigned n_emitted = 0;
+    for (int64_t item = (int64_t)blockIdx.x * kWalk4Warps + warp; item < a.items;
+         item += (int64_t)gridDim.x * kWalk4Warps) {
+        int64_t r = item;
+        const int tx = (int)(r % a.ntx);
+        r /= a.ntx;
+        const int ty = (int)(r % a.nty);
+        r /= a.nty;
+        const int64_t z = r % nz;
+        const int64_t w0 = (r / nz) * a.chunk, w1 = w0 + a.chunk < nw ? w0 + a.chunk : nw;
+        const int64_t y = (int64_t)ty * 30 - 1 + lane;
+        const int64_t xw = (int64_t)tx * 30 - 1;   // voxel of bit 0
+        const uint32_t xm = walk::x_exist_mask(xw, nx);
+        const uint32_t out = (lane >= 1 && lane <= 30) ? (xm & 0x7ffffffeu) : 0u;
+        // this lane's row of slice (w, zz); a row outside the image is all missing
+        auto load = [&](int64_t w, int64_t zz, uint32_t *P) {
+            if ((uint64_t)w < (uint64_t)nw && (uint64_t)zz < (uint64_t)nz && (uint64_t)y < (uint64_t)ny) {
+                const unsigned char *row = a.data + w * a.pitch[0] + zz * a.pitch[1] + y * a.pitch[2];
+                uint32_t words[K + 1];
+                const int sh = walk::load_row_words<K>(row, row_bytes, xw * (int64_t)sizeof(T), words);
+                walk::planes_from_words<K>(words, sh, P);
+                P[K] = ~xm;
+            } else {
 #pragma unroll
-        for (int ax = 0; ax < 4; ++ax) {
-            lo_ok[ax] = c[ax] > 0;
-            hi_ok[ax] = c[ax] + 1 < a.n[ax];
-        }
-        uint32_t win[3] = {0u, 0u, 0u};
-#pragma unroll
-        for (int dw = -1; dw <= 1; ++dw) {
-            const unsigned char *pw = pp + dw * a.pitch[0];
-            const bool okw = dw < 0 ? lo_ok[0] : (dw > 0 ? hi_ok[0] : true);
-#pragma unroll
-            for (int dz = -1; dz <= 1; ++dz) {
-                const unsigned char *pz = pw + dz * a.pitch[1];
-                const bool okz = okw && (dz < 0 ? lo_ok[1] : (dz > 0 ? hi_ok[1] : true));
-#pragma unroll
-                for (int dy = -1; dy <= 1; ++dy) {
-                    const unsigned char *py = pz + dy * a.pitch[2];
-                    const bool oky = okz && (dy < 0 ? lo_ok[2] : (dy > 0 ? hi_ok[2] : true));
-#pragma unroll
-                    for (int dx = -1; dx <= 1; ++dx) {
-                        const int k = (dw + 1) * 27 + (dz + 1) * 9 + (dy + 1) * 3 + (dx + 1);
-                        if (k == 40) continue;
-                        const bool ok = oky && (dx < 0 ? lo_ok[3] : (dx > 0 ? hi_ok[3] : true));
-                        // a neighbour later in memory: its first nonzero offset is positive
-                        const bool later = k > 40;
-                        bool beats = TOP;
-                        if (ok) {
-                            const int u = (int)__ldg(reinterpret_cast<const T *>(py) + dx);
-                            beats = TOP ? (later ? v <= u : v < u) : (later ? v >= u : v > u);
-                        }
-                        if (beats) win[k >> 5] |= 1u << (k & 31);
-                    }
-                }
+                for (int k = 0; k < K; ++k) P[k] = 0u;
+                P[K] = 0xffffffffu;
             }
-        }
-        int kappa = 0;
-#pragma unroll
-        for (int cell = 0; cell < kCells4; ++cell) {
-            const bool won = (win[0] & kCellMask[cell][0]) == kCellMask[cell][0] &&
-                             (win[1] & kCellMask[cell][1]) == kCellMask[cell][1] &&
-                             (win[2] & kCellMask[cell][2]) == kCellMask[cell][2];
-            kappa += won ? kCellSign[cell] : 0;
-        }
+        };
+        uint32_t Am[KP], A0[KP], Ap[KP];
+        uint32_t C[3][3][3];   // wins of slice (w, z) over hyperplane w-1
+        uint32_t unused[3][3];
         {
-            const int bin = v - a.h.lo;
-            const bool bad = kappa && a.range_check && (unsigned)bin >= (unsigned)a.h.nbins;
-            if (bad) atomicOr(a.status, DEV_RANGE);
-            const bool add = kappa && !bad;
-            // lanes adding to the same bin combine first (neighbouring voxels of
-            // a smooth field often share a gray level)
-            const unsigned act = __activemask();
-            const unsigned grp = __match_any_sync(act, add ? bin : -1 - (int)(threadIdx.x & 31));
-            const int sum = __reduce_add_sync(grp, kappa);
-            if (add && (int)(threadIdx.x & 31) == __ffs(grp) - 1 && sum) {
-                if (a.smem_hist)
-                    atomicAdd(&hist4[bin], sum);
-                else
-                    atomicAdd(a.h.acc + bin, (unsigned long long)(long long)sum);
+            uint32_t B0[KP];
+            load(w0 - 1, z - 1, Am);
+            load(w0 - 1, z, A0);
+            load(w0 - 1, z + 1, Ap);
+            load(w0, z, B0);
+            walk::slice_pair<K, TOP, false, true>(Am, B0, unused, C[0]);
+            walk::slice_pair<K, TOP, false, true>(A0, B0, unused, C[1]);
+            walk::slice_pair<K, TOP, false, true>(Ap, B0, unused, C[2]);
+#pragma unroll
+            for (int k = 0; k < KP; ++k) A0[k] = B0[k];
+            load(w0, z - 1, Am);
+            load(w0, z + 1, Ap);
+        }
+        for (int64_t w = w0; w < w1; ++w) {
+            // W0: wins of slice (w, z) in its hyperplane, as [dz][dy][dx]
+            uint32_t W[3][3][3];
+            walk::slice_pair<K, TOP, false, true>(Am, A0, unused, W[0]);
+            walk::in_slice<K, TOP>(A0, W[1]);
+            walk::slice_pair<K, TOP, true, false>(A0, Ap, W[2], unused);
+            uint32_t T0[4], Tm[4], Tp[4];
+            bs::kappa3d(W, T0);
+            const uint32_t bm = C[1][1][1];
+#pragma unroll
+            for (int i = 0; i < 27; ++i) (&C[0][0][0])[i] &= (&W[0][0][0])[i];
+            bs::kappa3d(C, Tm);
+            // hyperplane w+1: W becomes W0 & W+, C the wins of (w+1, z) over w
+            uint32_t B0[KP], Bm[KP], Bp[KP], fw[3][3];
+            load(w + 1, z, B0);
+            walk::slice_pair<K, TOP, true, true>(A0, B0, fw, C[1]);
+            const uint32_t bp = fw[1][1];
+#pragma unroll
+            for (int i = 0; i < 9; ++i) (&W[1][0][0])[i] &= (&fw[0][0])[i];
+            load(w + 1, z - 1, Bm);
+            walk::slice_pair<K, TOP, true, false>(A0, Bm, fw, unused);
+#pragma unroll
+            for (int i = 0; i < 9; ++i) (&W[0][0][0])[i] &= (&fw[0][0])[i];
+            load(w + 1, z + 1, Bp);
+            walk::slice_pair<K, TOP, true, false>(A0, Bp, fw, unused);
+#pragma unroll
+            for (int i = 0; i < 9; ++i) (&W[2][0][0])[i] &= (&fw[0][0])[i];
+            bs::kappa3d(W, Tp);
+            walk::slice_pair<K, TOP, false, true>(Am, B0, unused, C[0]);
+            walk::slice_pair<K, TOP, false, true>(Ap, B0, unused, C[2]);
+            uint32_t m = bs::kappa4_nonzero(T0, Tp, Tm, bp, bm) & ~A0[K] & out;
+            if (a.h.emitted) n_emitted += __popc(m);
+            while (m) {
+                const int i = __ffs(m) - 1;
+                m &= m - 1u;
+                // (-1)^4 = +1: the same sign in both complexes
+                bins.add(bs::bits_at<K>(A0, i), bs::kappa4_at(T0, Tp, Tm, bp, bm, i));
+            }
+#pragma unroll
+            for (int k = 0; k < KP; ++k) {
+                Am[k] = Bm[k];
+                A0[k] = B0[k];
+                Ap[k] = Bp[k];
             }
         }
+    }
+    if (a.h.emitted) {
+        const unsigned n = __reduce_add_sync(0xffffffffu, n_emitted);
+        if (lane == 0 && n) atomicAdd(a.h.emitted, (unsigned long long)n);
     }
     __syncthreads();
     if (a.smem_hist)
         for (int i = threadIdx.x; i < a.h.nbins; i += blockDim.x)
-            if (hist4[i]) atomicAdd(a.h.acc + i, (unsigned long long)(long long)hist4[i]);
-}
-
-// The 81 cells of four dimensions containing the voxel: axis subset A and a
-// side per axis of A; the neighbours are the nonempty sub-sums.
-void cell_tables(uint32_t mask[kCells4][3], int sign[kCells4])
-{
-    int c = 0;
-    for (int A = 0; A < 16; ++A) {
-        int axes[4], k = 0;
-        for (int ax = 0; ax < 4; ++ax)
-            if (A & (1 << ax)) axes[k++] = ax;
-        for (int s = 0; s < (1 << k); ++s) {
-            uint32_t m[3] = {0, 0, 0};
-            for (int B = 1; B < (1 << k); ++B) {
-                int d[4] = {0, 0, 0, 0};
-                for (int j = 0; j < k; ++j)
-                    if (B & (1 << j)) d[axes[j]] = (s & (1 << j)) ? 1 : -1;
-                const int idx = (d[0] + 1) * 27 + (d[1] + 1) * 9 + (d[2] + 1) * 3 + (d[3] + 1);
-                m[idx >> 5] |= 1u << (idx & 31);
-            }
-            mask[c][0] = m[0];
-            mask[c][1] = m[1];
-            mask[c][2] = m[2];
-            sign[c] = (k % 2 == 0) ? 1 : -1;
-            ++c;
-        }
-    }
-}
-
-cudaError_t upload_tables()
-{
-    static std::once_flag once;
-    static cudaError_t err = cudaSuccess;
-    std::call_once(once, [] {
-        uint32_t mask[kCells4][3];
-        int sign[kCells4];
-        cell_tables(mask, sign);
-        err = cudaMemcpyToSymbol(kCellMask, mask, sizeof(mask));
-        if (err == cudaSuccess) err = cudaMemcpyToSymbol(kCellSign, sign, sizeof(sign));
-    });
-    return err;
+            if (hist4w[i]) atomicAdd(a.h.acc + i, (unsigned long long)(long long)hist4w[i]);
 }
 
 template <typename T, bool TOP>
-cudaError_t launch4(const Nd4Args &a, int num_sms, size_t smem, cudaStream_t s)
+cudaError_t launch_walk4(Walk4Args a, int num_sms, size_t smem, cudaStream_t s)
 {
-    auto k = direct4d_kernel<T, TOP>;
+    auto k = walk4d_kernel<T, TOP>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    const int64_t total = a.n[0] * a.n[1] * a.n[2] * a.n[3];
-    const int64_t blocks = std::min<int64_t>((total + kNdThreads - 1) / kNdThreads, (int64_t)num_sms * 8);
-    k<<<(unsigned)blocks, kNdThreads, smem, s>>>(a);
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kWalk4Warps * 32, smem);
+    if (e != cudaSuccess) return e;
+    per_sm = std::max(per_sm, 1);
+    // w chunks: enough items for about two rounds of resident warps
+    a.ntx = (int32_t)((a.n[3] + 29) / 30);
+    a.nty = (int32_t)((a.n[2] + 29) / 30);
+    const int64_t base = a.n[1] * a.nty * a.ntx;
+    const int64_t target = 2LL * num_sms * per_sm * kWalk4Warps;
+    int64_t chunks = std::min<int64_t>(std::max<int64_t>((target + base - 1) / base, 1), a.n[0]);
+    a.chunk = (a.n[0] + chunks - 1) / chunks;
+    chunks = (a.n[0] + a.chunk - 1) / a.chunk;
+    a.items = chunks * base;
+    const int64_t blocks =
+        std::min<int64_t>((a.items + kWalk4Warps - 1) / kWalk4Warps, (int64_t)num_sms * per_sm);
+    k<<<(unsigned)blocks, kWalk4Warps * 32, smem, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -211,7 +215,7 @@ extern "C" ecc_status ecc_compute_nd(ecc_plan_t p, const ecc_image_nd *img, int6
     if (!d_ecc) return invalid("ecc_compute_nd: NULL output");
     if (img->dtype != p->d.dtype) return invalid("ecc_compute_nd: image dtype differs from the plan's dtype");
     const int es = img->dtype == ECC_U16 ? 2 : 1;
-    Nd4Args a{};
+    Walk4Args a{};
     a.data = static_cast<const unsigned char *>(img->data);
     int64_t nvox = 1;
     for (int ax = 0; ax < 4; ++ax) {
@@ -234,8 +238,6 @@ extern "C" ecc_status ecc_compute_nd(ecc_plan_t p, const ecc_image_nd *img, int6
         a.pitch[0] < (a.n[1] - 1) * a.pitch[1] + (a.n[2] - 1) * a.pitch[2] + a.n[3] * es)
         return invalid("ecc_compute_nd: pitches smaller than the extents they span");
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    cudaError_t e = upload_tables();
-    if (e != cudaSuccess) return cuda_fail(e, "ecc_compute_nd: cell tables");
     a.h = HistDst{p->acc, p->d.lo, p->nbins};
     if (p->d.flags & ECC_FLAG_COUNT_EMITTED) a.h.emitted = p->emitted;
     a.range_check = !(p->d.flags & ECC_FLAG_NO_RANGE_CHECK);
@@ -243,10 +245,10 @@ extern "C" ecc_status ecc_compute_nd(ecc_plan_t p, const ecc_image_nd *img, int6
     a.smem_hist = p->nbins <= kSmemBinsMax;
     const size_t smem = a.smem_hist ? sizeof(int) * (size_t)p->nbins : 0;
     const bool top = p->d.complex_mode == ECC_TOPCELL_MIN;
-    e = es == 1 ? (top ? launch4<unsigned char, true>(a, p->num_sms, smem, s)
-                       : launch4<unsigned char, false>(a, p->num_sms, smem, s))
-                : (top ? launch4<unsigned short, true>(a, p->num_sms, smem, s)
-                       : launch4<unsigned short, false>(a, p->num_sms, smem, s));
+    cudaError_t e = es == 1 ? (top ? launch_walk4<unsigned char, true>(a, p->num_sms, smem, s)
+                                   : launch_walk4<unsigned char, false>(a, p->num_sms, smem, s))
+                            : (top ? launch_walk4<unsigned short, true>(a, p->num_sms, smem, s)
+                                   : launch_walk4<unsigned short, false>(a, p->num_sms, smem, s));
     p->last_launches = 1;
     if (e == cudaSuccess) {
         e = launch_scan(p->acc, reinterpret_cast<long long *>(d_ecc), reinterpret_cast<long long *>(d_vcec), 1,

@@ -433,5 +433,89 @@ struct Walk2d {
     }
 };
 
+// ------------------------------------------------------------------ 4D
+//
+// Slices: a 4D image is a stack of 2D (y, x) slices indexed by (w, z); a
+// warp holds a slice as lane-packed rows (lane l: row y0-1+l, planes 0..K-1
+// the value, plane K set where the voxel is missing).  Comparisons take the
+// existence plane as the most significant bit (a missing voxel is 2^K).
+
+// Wins between slices X and Y, every voxel of X earlier in memory than
+// every voxel of Y (X lies at a smaller w, or the same w and a smaller z):
+//   f[dy][dx]: X(y, x) beats Y(y+dy-1, x+dx-1)        (when FWD)
+//   r[dy][dx]: Y(y, x) beats X(y+dy-1, x+dx-1)        (when REV)
+// Nine comparisons per lane: X(y) against Y(y) (R0), X(y-1) against Y(y)
+// (G) and X(y+1) against Y(y) (K2), at the three x offsets; the rest are
+// neighbouring lanes' results or the complements of shifted ones.
+// Warp-collective.
+template <int K, bool TOP, bool FWD, bool REV>
+__device__ __forceinline__ void slice_pair(const uint32_t *X, const uint32_t *Y, uint32_t f[3][3], uint32_t r[3][3])
+{
+    constexpr int KP = K + 1;
+    uint32_t Yp[KP], Ym[KP], XD[KP], XU[KP];
+    shifted<KP>(Y, Yp, Ym);
+#pragma unroll
+    for (int k = 0; k < KP; ++k) {
+        XD[k] = from_prev_lane(X[k]);
+        XU[k] = from_next_lane(X[k]);
+    }
+    // [d] at bit x: against Y(., x+d-1)
+    uint32_t R0[3], G[3], K2[3];
+    R0[0] = beats_later<KP, TOP>(X, Ym);
+    R0[1] = beats_later<KP, TOP>(X, Y);
+    R0[2] = beats_later<KP, TOP>(X, Yp);
+    G[0] = beats_later<KP, TOP>(XD, Ym);
+    G[1] = beats_later<KP, TOP>(XD, Y);
+    G[2] = beats_later<KP, TOP>(XD, Yp);
+    K2[0] = beats_later<KP, TOP>(XU, Ym);
+    K2[1] = beats_later<KP, TOP>(XU, Y);
+    K2[2] = beats_later<KP, TOP>(XU, Yp);
+    if (FWD) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            f[0][d] = from_prev_lane(K2[d]);   // lane y-1: X(y) vs Y(y-1)
+            f[1][d] = R0[d];
+            f[2][d] = from_next_lane(G[d]);    // lane y+1: X(y) vs Y(y+1)
+        }
+    }
+    if (REV) {
+        r[0][0] = ~at_offset<-1>(G[2]);
+        r[0][1] = ~G[1];
+        r[0][2] = ~at_offset<+1>(G[0]);
+        r[1][0] = ~at_offset<-1>(R0[2]);
+        r[1][1] = ~R0[1];
+        r[1][2] = ~at_offset<+1>(R0[0]);
+        r[2][0] = ~at_offset<-1>(K2[2]);
+        r[2][1] = ~K2[1];
+        r[2][2] = ~at_offset<+1>(K2[0]);
+    }
+}
+
+// Wins of the voxels of slice A over their eight neighbours in the slice:
+// a[dy][dx]: A(y, x) beats A(y+dy-1, x+dx-1); a[1][1] = 0.  Warp-collective.
+template <int K, bool TOP>
+__device__ __forceinline__ void in_slice(const uint32_t *A, uint32_t a[3][3])
+{
+    constexpr int KP = K + 1;
+    uint32_t Ap[KP], Am[KP], U[KP];
+    shifted<KP>(A, Ap, Am);
+#pragma unroll
+    for (int k = 0; k < KP; ++k) U[k] = from_next_lane(A[k]);
+    // E[x]: A(y, x-1) vs A(y, x); F[d][x]: A(y, x+1-d) vs A(y+1, x)
+    const uint32_t E = beats_later<KP, TOP>(Am, A);
+    const uint32_t F0 = beats_later<KP, TOP>(Ap, U);
+    const uint32_t F1 = beats_later<KP, TOP>(A, U);
+    const uint32_t F2 = beats_later<KP, TOP>(Am, U);
+    a[1][0] = ~E;
+    a[1][1] = 0u;
+    a[1][2] = at_offset<+1>(E);
+    a[2][0] = at_offset<-1>(F0);
+    a[2][1] = F1;
+    a[2][2] = at_offset<+1>(F2);
+    a[0][0] = ~from_prev_lane(F2);
+    a[0][1] = ~from_prev_lane(F1);
+    a[0][2] = ~from_prev_lane(F0);
+}
+
 }  // namespace walk
 }  // namespace ecc

@@ -32,6 +32,16 @@ void h_kappa3d_many(const uint32_t *w27, int64_t n, uint32_t *T, uint32_t *nz)
     }
 }
 
+// w81: 81 masks in [dw][dz][dy][dx] order; writes kappa4 of each of the 32 voxels; returns nonzero mask
+uint32_t h_kappa4d(const uint32_t *w81, int32_t *kappa)
+{
+    uint32_t w[3][3][3][3], T0[4], Tp[4], Tm[4], bp, bm;
+    for (int i = 0; i < 81; ++i) (&w[0][0][0][0])[i] = w81[i];
+    const uint32_t nz = kappa4d(w, T0, Tp, Tm, bp, bm);
+    for (int i = 0; i < 32; ++i) kappa[i] = kappa4_at(T0, Tp, Tm, bp, bm, i);
+    return nz;
+}
+
 void h_count12(const uint32_t *x, uint32_t *o) { count12(x, o); }
 
 // w: 9 masks in [dy][dx] order; writes X[3] (kappa = X0 + X1 + 2 X2 - 3); returns nonzero mask

@@ -2,6 +2,7 @@
 (transpose to bit planes, bit-serial comparison, carry-save counting and the
 per-voxel cell count), each against naive per-voxel Python."""
 import ctypes
+import itertools
 import subprocess
 from pathlib import Path
 
@@ -185,3 +186,41 @@ def test_kappa2d(h):
                         kap += w[a, 1] & w[1, b] & w[a, b]
                 assert xs[0] + xs[1] + 2 * xs[2] - 3 == kap
                 assert ((nz >> x) & 1) == (kap != 0)
+
+
+def _kappa4_scalar(w):
+    """1 - edges + squares - cubes + tesseracts over the 81 cells of 4D
+    containing the voxel, from the 80 wins w[dw][dz][dy][dx] (0/1): a cell
+    (axis subset A, a side per axis) is won when every nonempty sub-sum of
+    its sides is."""
+    k = 0
+    for A in itertools.product((0, 1), repeat=4):
+        axes = [i for i in range(4) if A[i]]
+        for sides in itertools.product((-1, 1), repeat=len(axes)):
+            won = 1
+            for B in itertools.product((0, 1), repeat=len(axes)):
+                if not any(B):
+                    continue
+                d = [0, 0, 0, 0]
+                for j, ax in enumerate(axes):
+                    if B[j]:
+                        d[ax] = sides[j]
+                won &= w[d[0] + 1, d[1] + 1, d[2] + 1, d[3] + 1]
+            k += (-1) ** len(axes) * won
+    return k
+
+
+def test_kappa4d_against_the_81_cells(h):
+    rng = np.random.default_rng(6)
+    h.h_kappa4d.argtypes = [ctypes.POINTER(ctypes.c_uint32), ctypes.POINTER(ctypes.c_int32)]
+    h.h_kappa4d.restype = ctypes.c_uint32
+    for density in (0.2, 0.5, 0.8, 0.95, 0.99):
+        for _ in range(12):
+            bits = (rng.uniform(size=(81, 32)) < density).astype(np.uint64)
+            w81 = np.array([sum(int(bits[i, x]) << x for x in range(32)) for i in range(81)], np.uint32)
+            kap = np.zeros(32, np.int32)
+            nz = h.h_kappa4d(_p(w81), kap.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)))
+            for x in range(32):
+                want = _kappa4_scalar(bits[:, x].reshape(3, 3, 3, 3).astype(int))
+                assert kap[x] == want
+                assert ((nz >> x) & 1) == (want != 0)

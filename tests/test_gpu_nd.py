@@ -52,6 +52,19 @@ def test_smoothed_4d_u8_and_u16(mode):
     assert np.array_equal(_run(torch.from_numpy(img16).cuda(), 0, 1023, mode), oracle.ecc(img16, 0, 1023, mode))
 
 
+@pytest.mark.parametrize("mode", list(MODES))
+def test_4d_row_tiles_windows_and_w_chunks(mode):
+    """Shapes spanning several 30-row tiles and 30-column windows with
+    ragged tails, and (the first) enough (z, tile, window) columns that the
+    w axis is cut into chunks of several hyperplanes with a short last one."""
+    rng = np.random.default_rng(85)
+    for shape, levels, dt, hi in [((40, 64, 40, 40), 7, np.uint8, 255), ((9, 5, 65, 70), 3, np.uint8, 255),
+                                  ((6, 7, 33, 95), 300, np.uint16, 1023), ((7, 3, 31, 61), 4, np.uint16, 65535)]:
+        img = rng.integers(0, levels, size=shape).astype(dt)
+        got = _run(torch.from_numpy(img).cuda(), 0, hi, mode)
+        assert np.array_equal(got, oracle.ecc(img, 0, hi, mode)), (shape, levels)
+
+
 def test_pitched_4d_view():
     rng = np.random.default_rng(83)
     base = rng.integers(0, 6, size=(6, 9, 11, 40)).astype(np.uint8)
