@@ -32,8 +32,9 @@ namespace {
 //   kappa4 = k3(W0) - b+ k3(W0 & W+) - b- k3(W0 & W-)
 // with W0, W+, W- its wins over hyperplanes w, w+1, w-1, b+- its wins over
 // its two w-neighbours and k3 the 3D count (bs::kappa4_nonzero).  Each warp
-// takes one (z, 30-row tile, 30-column window) column over a chunk of w: it
-// holds slices (w, z-1..z+1), loads (w+1, z-1..z+1) at every step, and
+// takes one (z, 30-row tile, 30-column window) column over a chunk of w
+// (or several partial tiles side by side): it holds slices (w, z-1..z+1),
+// loads (w+1, z-1..z+1) at every step, and
 // compares slices in blocks of nine directions (walk::slice_pair), each
 // pair of voxels at most once per warp.  The wins over hyperplane w-1 are
 // the complements carried from the step before.
@@ -43,9 +44,14 @@ struct Walk4Args {
     const unsigned char *data;
     int64_t n[4];        // w, z, y, x
     int64_t pitch[3];    // bytes: w, z, y
-    int64_t items;       // w chunks x nz x row tiles x windows
-    int32_t ntx, nty;    // windows of 30 columns, tiles of 30 rows
+    int64_t items;       // w chunks x per_chunk
     int64_t chunk;       // hyperplanes per item
+    int64_t per_chunk;   // items per w chunk: full_items, then the packed ones
+    int64_t full_items;  // nz x full row tiles x windows
+    int32_t ntx;         // windows of 30 columns
+    int32_t nty_full;    // tiles of 30 rows
+    int32_t remy;        // rows left below the full tiles (0..29)
+    int32_t pack;        // partial tiles (remy rows + 2 halo lanes) per warp
     HistDst h;
     int32_t smem_hist, range_check;
     unsigned int *status;
@@ -66,17 +72,35 @@ __global__ void __launch_bounds__(kWalk4Warps * 32) walk4d_kernel(const Walk4Arg
     unsigned n_emitted = 0;
     for (int64_t item = (int64_t)blockIdx.x * kWalk4Warps + warp; item < a.items;
          item += (int64_t)gridDim.x * kWalk4Warps) {
-        int64_t r = item;
-        const int tx = (int)(r % a.ntx);
-        r /= a.ntx;
-        const int ty = (int)(r % a.nty);
-        r /= a.nty;
-        const int64_t z = r % nz;
-        const int64_t w0 = (r / nz) * a.chunk, w1 = w0 + a.chunk < nw ? w0 + a.chunk : nw;
-        const int64_t y = (int64_t)ty * 30 - 1 + lane;
+        // Full items: lane l holds row 30 ty - 1 + l of column (z, tx).  Packed
+        // items: the last remy rows of `pack` columns side by side, remy + 2
+        // lanes each (a halo lane on either side), so a partial tile does not
+        // take a whole warp.
+        const int64_t ci = item / a.per_chunk;
+        int64_t r = item - ci * a.per_chunk;
+        const int64_t w0 = ci * a.chunk, w1 = w0 + a.chunk < nw ? w0 + a.chunk : nw;
+        int64_t z, y;
+        int tx;
+        bool lane_out;
+        if (r < a.full_items) {
+            tx = (int)(r % a.ntx);
+            r /= a.ntx;
+            const int ty = (int)(r % a.nty_full);
+            z = r / a.nty_full;
+            y = (int64_t)ty * 30 - 1 + lane;
+            lane_out = lane >= 1 && lane <= 30;
+        } else {
+            const int seg_len = a.remy + 2, seg = lane / seg_len, j = lane - seg * seg_len;
+            const int64_t c = (r - a.full_items) * a.pack + seg;
+            const bool valid = seg < a.pack && c < nz * a.ntx;
+            z = valid ? c / a.ntx : 0;
+            tx = valid ? (int)(c % a.ntx) : 0;
+            y = valid ? (int64_t)a.nty_full * 30 - 1 + j : -2;   // -2: no row
+            lane_out = valid && j >= 1 && j <= a.remy;
+        }
         const int64_t xw = (int64_t)tx * 30 - 1;   // voxel of bit 0
         const uint32_t xm = walk::x_exist_mask(xw, nx);
-        const uint32_t out = (lane >= 1 && lane <= 30) ? (xm & 0x7ffffffeu) : 0u;
+        const uint32_t out = lane_out ? (xm & 0x7ffffffeu) : 0u;
         // this lane's row of slice (w, zz); a row outside the image is all missing
         auto load = [&](int64_t w, int64_t zz, uint32_t *P) {
             if ((uint64_t)w < (uint64_t)nw && (uint64_t)zz < (uint64_t)nz && (uint64_t)y < (uint64_t)ny) {
@@ -176,15 +200,32 @@ cudaError_t launch_walk4(Walk4Args a, int num_sms, size_t smem, cudaStream_t s)
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kWalk4Warps * 32, smem);
     if (e != cudaSuccess) return e;
     per_sm = std::max(per_sm, 1);
-    // w chunks: enough items for about two rounds of resident warps
+    // w chunks of c hyperplanes: an item costs c + 1 steps (one to fill the
+    // state), each warp runs ceil(items / resident warps) items; take the c
+    // with the least of (rounds x steps), the longest any warp runs.
     a.ntx = (int32_t)((a.n[3] + 29) / 30);
-    a.nty = (int32_t)((a.n[2] + 29) / 30);
-    const int64_t base = a.n[1] * a.nty * a.ntx;
-    const int64_t target = 2LL * num_sms * per_sm * kWalk4Warps;
-    int64_t chunks = std::min<int64_t>(std::max<int64_t>((target + base - 1) / base, 1), a.n[0]);
-    a.chunk = (a.n[0] + chunks - 1) / chunks;
-    chunks = (a.n[0] + a.chunk - 1) / a.chunk;
-    a.items = chunks * base;
+    a.nty_full = (int32_t)(a.n[2] / 30);
+    a.remy = (int32_t)(a.n[2] % 30);
+    a.pack = 32 / (a.remy + 2);
+    a.full_items = a.n[1] * a.nty_full * a.ntx;
+    a.per_chunk = a.full_items + (a.remy ? (a.n[1] * a.ntx + a.pack - 1) / a.pack : 0);
+    const int64_t base = a.per_chunk;
+    const int64_t resident = (int64_t)num_sms * per_sm * kWalk4Warps;
+    int64_t best_c = a.n[0], best_cost = -1;
+    // chunk counts k = 1, 2, ... until there are far more items than warps
+    for (int64_t k = 1; k <= a.n[0]; ++k) {
+        const int64_t c = (a.n[0] + k - 1) / k;
+        const int64_t chunks = (a.n[0] + c - 1) / c;
+        const int64_t rounds = (chunks * base + resident - 1) / resident;
+        const int64_t cost = rounds * (c + 1);
+        if (best_cost < 0 || cost < best_cost) {
+            best_cost = cost;
+            best_c = c;
+        }
+        if (chunks * base > 64 * resident) break;
+    }
+    a.chunk = best_c;
+    a.items = ((a.n[0] + best_c - 1) / best_c) * base;
     const int64_t blocks =
         std::min<int64_t>((a.items + kWalk4Warps - 1) / kWalk4Warps, (int64_t)num_sms * per_sm);
     k<<<(unsigned)blocks, kWalk4Warps * 32, smem, s>>>(a);
