@@ -31,14 +31,22 @@ namespace {
 // and those cells extended to w+1 or w-1, so its count is
 //   kappa4 = k3(W0) - b+ k3(W0 & W+) - b- k3(W0 & W-)
 // with W0, W+, W- its wins over hyperplanes w, w+1, w-1, b+- its wins over
-// its two w-neighbours and k3 the 3D count (bs::kappa4_nonzero).  Each warp
-// takes one (z, 30-row tile, 30-column window) column over a chunk of w
-// (or several partial tiles side by side): it holds slices (w, z-1..z+1),
-// loads (w+1, z-1..z+1) at every step, and
-// compares slices in blocks of nine directions (walk::slice_pair), each
-// pair of voxels at most once per warp.  The wins over hyperplane w-1 are
-// the complements carried from the step before.
-constexpr int kWalk4Warps = 4;
+// its two w-neighbours and k3 the 3D count (bs::kappa4_nonzero).
+//
+// A CTA of kZ warps takes kZ consecutive z over one (30-row tile,
+// 30-column window) column and a chunk of w (or several partial row tiles
+// side by side); warp i holds z0 + i, lanes hold the rows (the 3D walker's
+// layout).  At every step the CTA loads hyperplane w+1 (its kZ slices and
+// the two halo slices z0-1, z0+kZ) into shared memory once, and each pair
+// of neighbouring slices is compared once (walk::slice_pair, nine
+// directions per block): warp i compares its slice (w, z) with (w+1, z-1),
+// (w+1, z), (w+1, z+1) and slice (w+1, z) with (w+1, z+1); the reverse
+// halves it does not need itself go through shared memory to the warps of
+// z-1 and z+1, which read them at the next step (one __syncthreads a step;
+// slices triple-buffered, exchanged wins double-buffered, by step).  The
+// halo pairs are spread over warps 1 and 2; warps 0 and kZ-1 load the halo
+// slices.
+constexpr int kZ = 4;
 
 struct Walk4Args {
     const unsigned char *data;
@@ -47,7 +55,8 @@ struct Walk4Args {
     int64_t items;       // w chunks x per_chunk
     int64_t chunk;       // hyperplanes per item
     int64_t per_chunk;   // items per w chunk: full_items, then the packed ones
-    int64_t full_items;  // nz x full row tiles x windows
+    int64_t full_items;  // z groups x full row tiles x windows
+    int64_t ngz;         // groups of kZ consecutive z
     int32_t ntx;         // windows of 30 columns
     int32_t nty_full;    // tiles of 30 rows
     int32_t remy;        // rows left below the full tiles (0..29)
@@ -57,47 +66,79 @@ struct Walk4Args {
     unsigned int *status;
 };
 
+// Shared-memory words before the histogram: slices of three hyperplanes
+// (kZ + 2 each, KP planes) and three double-buffered win exchanges.
+__host__ __device__ constexpr int walk4_slice_words(int KP) { return 3 * (kZ + 2) * KP * 32; }
+__host__ __device__ constexpr int walk4_xchg_words() { return 2 * kZ * 9 * 32; }
+__host__ __device__ constexpr int walk4_words(int KP) { return walk4_slice_words(KP) + 3 * walk4_xchg_words(); }
+
 template <typename T, bool TOP>
-__global__ void __launch_bounds__(kWalk4Warps * 32) walk4d_kernel(const Walk4Args a)
+__global__ void __launch_bounds__(kZ * 32) walk4d_kernel(const Walk4Args a)
 {
     constexpr int K = 8 * sizeof(T), KP = K + 1;
-    extern __shared__ int hist4w[];
+    extern __shared__ uint32_t smem4[];
+    uint32_t *const SL = smem4;                                   // [3][kZ + 2][KP][32]
+    uint32_t *const MZ = SL + walk4_slice_words(KP);              // [2][kZ][9][32]
+    uint32_t *const CM = MZ + walk4_xchg_words();
+    uint32_t *const CP = CM + walk4_xchg_words();
+    int *const hist = reinterpret_cast<int *>(CP + walk4_xchg_words());
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (a.smem_hist)
-        for (int i = threadIdx.x; i < a.h.nbins; i += blockDim.x) hist4w[i] = 0;
-    __syncthreads();
-    const walk::Bins bins{a.smem_hist ? hist4w : nullptr, a.h.acc, a.h.lo, a.h.nbins, a.range_check, a.status};
+        for (int i = threadIdx.x; i < a.h.nbins; i += blockDim.x) hist[i] = 0;
+    const walk::Bins bins{a.smem_hist ? hist : nullptr, a.h.acc, a.h.lo, a.h.nbins, a.range_check, a.status};
     const int64_t nw = a.n[0], nz = a.n[1], ny = a.n[2], nx = a.n[3];
     const int64_t row_bytes = nx * (int64_t)sizeof(T);
     unsigned n_emitted = 0;
-    for (int64_t item = (int64_t)blockIdx.x * kWalk4Warps + warp; item < a.items;
-         item += (int64_t)gridDim.x * kWalk4Warps) {
-        // Full items: lane l holds row 30 ty - 1 + l of column (z, tx).  Packed
-        // items: the last remy rows of `pack` columns side by side, remy + 2
-        // lanes each (a halo lane on either side), so a partial tile does not
-        // take a whole warp.
+
+    // slot j of hyperplane buffer h holds slice z0 - 1 + j; plane k at [k * 32]
+    auto slot = [&](int h, int j) { return SL + (h * (kZ + 2) + j) * KP * 32 + lane; };
+    auto put_slice = [&](int h, int j, const uint32_t *P) {
+        uint32_t *d = slot(h, j);
+#pragma unroll
+        for (int k = 0; k < KP; ++k) d[k * 32] = P[k];
+    };
+    auto get_slice = [&](int h, int j, uint32_t *P) {
+        const uint32_t *d = slot(h, j);
+#pragma unroll
+        for (int k = 0; k < KP; ++k) P[k] = d[k * 32];
+    };
+    auto xchg = [&](uint32_t *base, int par, int i) { return base + (par * kZ + i) * 9 * 32 + lane; };
+    auto put9 = [&](uint32_t *d, const uint32_t m[3][3]) {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) d[i * 32] = (&m[0][0])[i];
+    };
+    auto get9 = [&](const uint32_t *d, uint32_t m[3][3]) {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) (&m[0][0])[i] = d[i * 32];
+    };
+
+    for (int64_t item = blockIdx.x; item < a.items; item += gridDim.x) {
+        // Full items: lane l holds row 30 ty - 1 + l of column (z group,
+        // window).  Packed items: the last remy rows of `pack` columns side
+        // by side, remy + 2 lanes each (a halo lane on either side).
         const int64_t ci = item / a.per_chunk;
         int64_t r = item - ci * a.per_chunk;
         const int64_t w0 = ci * a.chunk, w1 = w0 + a.chunk < nw ? w0 + a.chunk : nw;
-        int64_t z, y;
+        int64_t z0, y;
         int tx;
         bool lane_out;
         if (r < a.full_items) {
             tx = (int)(r % a.ntx);
             r /= a.ntx;
             const int ty = (int)(r % a.nty_full);
-            z = r / a.nty_full;
+            z0 = (r / a.nty_full) * kZ;
             y = (int64_t)ty * 30 - 1 + lane;
             lane_out = lane >= 1 && lane <= 30;
         } else {
             const int seg_len = a.remy + 2, seg = lane / seg_len, j = lane - seg * seg_len;
             const int64_t c = (r - a.full_items) * a.pack + seg;
-            const bool valid = seg < a.pack && c < nz * a.ntx;
-            z = valid ? c / a.ntx : 0;
+            const bool valid = seg < a.pack && c < a.ngz * a.ntx;
+            z0 = valid ? (c / a.ntx) * kZ : 0;
             tx = valid ? (int)(c % a.ntx) : 0;
             y = valid ? (int64_t)a.nty_full * 30 - 1 + j : -2;   // -2: no row
             lane_out = valid && j >= 1 && j <= a.remy;
         }
+        const int64_t z = z0 + warp;
         const int64_t xw = (int64_t)tx * 30 - 1;   // voxel of bit 0
         const uint32_t xm = walk::x_exist_mask(xw, nx);
         const uint32_t out = lane_out ? (xm & 0x7ffffffeu) : 0u;
@@ -115,67 +156,110 @@ __global__ void __launch_bounds__(kWalk4Warps * 32) walk4d_kernel(const Walk4Arg
                 P[K] = 0xffffffffu;
             }
         };
-        uint32_t Am[KP], A0[KP], Ap[KP];
-        uint32_t C[3][3][3];   // wins of slice (w, z) over hyperplane w-1
-        uint32_t unused[3][3];
-        {
+        // hyperplane slots of this CTA's z range, halos from warps 0 and kZ-1
+        auto load_hyperplane = [&](int64_t w, int h, uint32_t *own) {
+            load(w, z, own);
+            put_slice(h, warp + 1, own);
+            if (warp == 0 || warp == kZ - 1) {
+                uint32_t H[KP];
+                const int j = warp == 0 ? 0 : kZ + 1;
+                load(w, z0 - 1 + j, H);
+                put_slice(h, j, H);
+            }
+        };
+
+        __syncthreads();   // the previous item's readers are done with every buffer
+        uint32_t A0[KP];
+        load_hyperplane(w0 - 1, 0, A0);
+        uint32_t W2[3][3], C1[3][3];   // carried: W0 layer z+1 and W- layer z of the next output
+        int hA = 0;
+        for (int64_t w = w0 - 1; w < w1; ++w) {
+            const int hB = hA == 2 ? 0 : hA + 1;
+            const int par = (int)((w - w0 + 1) & 1), prv = par ^ 1;
             uint32_t B0[KP];
-            load(w0 - 1, z - 1, Am);
-            load(w0 - 1, z, A0);
-            load(w0 - 1, z + 1, Ap);
-            load(w0, z, B0);
-            walk::slice_pair<K, TOP, false, true>(Am, B0, unused, C[0]);
-            walk::slice_pair<K, TOP, false, true>(A0, B0, unused, C[1]);
-            walk::slice_pair<K, TOP, false, true>(Ap, B0, unused, C[2]);
+            load_hyperplane(w + 1, hB, B0);
+            __syncthreads();
+            const bool emit_step = w >= w0;   // the first step only fills the carried state
+            uint32_t W[3][3][3], T0[4], Tm[4], Tp[4], bm = 0, bp = 0;
+            if (emit_step) {
+                // W0 of slice (w, z), then its wins over hyperplane w-1
+                get9(xchg(MZ, prv, warp), W[0]);
+                walk::in_slice<K, TOP>(A0, W[1]);
+#pragma unroll
+                for (int i = 0; i < 9; ++i) (&W[2][0][0])[i] = (&W2[0][0])[i];
+                bs::kappa3d(W, T0);
+                uint32_t C[3][3][3];
+                get9(xchg(CM, prv, warp), C[0]);
+                get9(xchg(CP, prv, warp), C[2]);
+#pragma unroll
+                for (int i = 0; i < 9; ++i) (&C[1][0][0])[i] = (&C1[0][0])[i];
+                bm = C[1][1][1];
+#pragma unroll
+                for (int i = 0; i < 27; ++i) (&C[0][0][0])[i] &= (&W[0][0][0])[i];
+                bs::kappa3d(C, Tm);
+            }
+            uint32_t fw[3][3], rv[3][3];
+            {
+                // (w, z) against (w+1, z-1): W+ layer z-1; the reverse is W- layer z+1 of warp z-1
+                uint32_t Bm[KP];
+                get_slice(hB, warp, Bm);
+                walk::slice_pair<K, TOP, true, true>(A0, Bm, fw, rv);
+                if (warp > 0) put9(xchg(CP, par, warp - 1), rv);
+                if (emit_step)
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) (&W[0][0][0])[i] &= (&fw[0][0])[i];
+            }
+            // (w, z) against (w+1, z): W+ layer z and this warp's next W- layer z
+            walk::slice_pair<K, TOP, true, true>(A0, B0, fw, C1);
+            bp = fw[1][1];
+            if (emit_step)
+#pragma unroll
+                for (int i = 0; i < 9; ++i) (&W[1][0][0])[i] &= (&fw[0][0])[i];
+            {
+                uint32_t Bp[KP];
+                get_slice(hB, warp + 2, Bp);
+                // (w, z) against (w+1, z+1): W+ layer z+1; the reverse is W- layer z-1 of warp z+1
+                walk::slice_pair<K, TOP, true, true>(A0, Bp, fw, rv);
+                if (warp < kZ - 1) put9(xchg(CM, par, warp + 1), rv);
+                if (emit_step)
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) (&W[2][0][0])[i] &= (&fw[0][0])[i];
+                // (w+1, z) against (w+1, z+1): next W0 layer z+1; the reverse is warp z+1's layer z-1
+                walk::slice_pair<K, TOP, true, true>(B0, Bp, W2, rv);
+                if (warp < kZ - 1) put9(xchg(MZ, par, warp + 1), rv);
+            }
+            // the halo pairs of warps 0 and kZ-1
+            if (warp == 1) {
+                uint32_t X[KP], Y[KP];
+                get_slice(hB, 0, X);
+                get_slice(hB, 1, Y);
+                walk::slice_pair<K, TOP, false, true>(X, Y, fw, rv);
+                put9(xchg(MZ, par, 0), rv);
+            } else if (warp == 2) {
+                uint32_t X[KP], Y[KP];
+                get_slice(hA, 0, X);
+                get_slice(hB, 1, Y);
+                walk::slice_pair<K, TOP, false, true>(X, Y, fw, rv);
+                put9(xchg(CM, par, 0), rv);
+                get_slice(hA, kZ + 1, X);
+                get_slice(hB, kZ, Y);
+                walk::slice_pair<K, TOP, false, true>(X, Y, fw, rv);
+                put9(xchg(CP, par, kZ - 1), rv);
+            }
+            if (emit_step) {
+                bs::kappa3d(W, Tp);
+                uint32_t m = bs::kappa4_nonzero(T0, Tp, Tm, bp, bm) & ~A0[K] & out;
+                if (a.h.emitted) n_emitted += __popc(m);
+                while (m) {
+                    const int i = __ffs(m) - 1;
+                    m &= m - 1u;
+                    // (-1)^4 = +1: the same sign in both complexes
+                    bins.add(bs::bits_at<K>(A0, i), bs::kappa4_at(T0, Tp, Tm, bp, bm, i));
+                }
+            }
 #pragma unroll
             for (int k = 0; k < KP; ++k) A0[k] = B0[k];
-            load(w0, z - 1, Am);
-            load(w0, z + 1, Ap);
-        }
-        for (int64_t w = w0; w < w1; ++w) {
-            // W0: wins of slice (w, z) in its hyperplane, as [dz][dy][dx]
-            uint32_t W[3][3][3];
-            walk::slice_pair<K, TOP, false, true>(Am, A0, unused, W[0]);
-            walk::in_slice<K, TOP>(A0, W[1]);
-            walk::slice_pair<K, TOP, true, false>(A0, Ap, W[2], unused);
-            uint32_t T0[4], Tm[4], Tp[4];
-            bs::kappa3d(W, T0);
-            const uint32_t bm = C[1][1][1];
-#pragma unroll
-            for (int i = 0; i < 27; ++i) (&C[0][0][0])[i] &= (&W[0][0][0])[i];
-            bs::kappa3d(C, Tm);
-            // hyperplane w+1: W becomes W0 & W+, C the wins of (w+1, z) over w
-            uint32_t B0[KP], Bm[KP], Bp[KP], fw[3][3];
-            load(w + 1, z, B0);
-            walk::slice_pair<K, TOP, true, true>(A0, B0, fw, C[1]);
-            const uint32_t bp = fw[1][1];
-#pragma unroll
-            for (int i = 0; i < 9; ++i) (&W[1][0][0])[i] &= (&fw[0][0])[i];
-            load(w + 1, z - 1, Bm);
-            walk::slice_pair<K, TOP, true, false>(A0, Bm, fw, unused);
-#pragma unroll
-            for (int i = 0; i < 9; ++i) (&W[0][0][0])[i] &= (&fw[0][0])[i];
-            load(w + 1, z + 1, Bp);
-            walk::slice_pair<K, TOP, true, false>(A0, Bp, fw, unused);
-#pragma unroll
-            for (int i = 0; i < 9; ++i) (&W[2][0][0])[i] &= (&fw[0][0])[i];
-            bs::kappa3d(W, Tp);
-            walk::slice_pair<K, TOP, false, true>(Am, B0, unused, C[0]);
-            walk::slice_pair<K, TOP, false, true>(Ap, B0, unused, C[2]);
-            uint32_t m = bs::kappa4_nonzero(T0, Tp, Tm, bp, bm) & ~A0[K] & out;
-            if (a.h.emitted) n_emitted += __popc(m);
-            while (m) {
-                const int i = __ffs(m) - 1;
-                m &= m - 1u;
-                // (-1)^4 = +1: the same sign in both complexes
-                bins.add(bs::bits_at<K>(A0, i), bs::kappa4_at(T0, Tp, Tm, bp, bm, i));
-            }
-#pragma unroll
-            for (int k = 0; k < KP; ++k) {
-                Am[k] = Bm[k];
-                A0[k] = B0[k];
-                Ap[k] = Bp[k];
-            }
+            hA = hB;
         }
     }
     if (a.h.emitted) {
@@ -185,36 +269,38 @@ __global__ void __launch_bounds__(kWalk4Warps * 32) walk4d_kernel(const Walk4Arg
     __syncthreads();
     if (a.smem_hist)
         for (int i = threadIdx.x; i < a.h.nbins; i += blockDim.x)
-            if (hist4w[i]) atomicAdd(a.h.acc + i, (unsigned long long)(long long)hist4w[i]);
+            if (hist[i]) atomicAdd(a.h.acc + i, (unsigned long long)(long long)hist[i]);
 }
 
 template <typename T, bool TOP>
-cudaError_t launch_walk4(Walk4Args a, int num_sms, size_t smem, cudaStream_t s)
+cudaError_t launch_walk4(Walk4Args a, int num_sms, cudaStream_t s)
 {
+    constexpr int KP = 8 * sizeof(T) + 1;
     auto k = walk4d_kernel<T, TOP>;
+    const size_t smem = sizeof(uint32_t) * (size_t)walk4_words(KP) + (a.smem_hist ? sizeof(int) * (size_t)a.h.nbins : 0);
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
     int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kWalk4Warps * 32, smem);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, kZ * 32, smem);
     if (e != cudaSuccess) return e;
     per_sm = std::max(per_sm, 1);
-    // w chunks of c hyperplanes: an item costs c + 1 steps (one to fill the
-    // state), each warp runs ceil(items / resident warps) items; take the c
-    // with the least of (rounds x steps), the longest any warp runs.
     a.ntx = (int32_t)((a.n[3] + 29) / 30);
     a.nty_full = (int32_t)(a.n[2] / 30);
     a.remy = (int32_t)(a.n[2] % 30);
     a.pack = 32 / (a.remy + 2);
-    a.full_items = a.n[1] * a.nty_full * a.ntx;
-    a.per_chunk = a.full_items + (a.remy ? (a.n[1] * a.ntx + a.pack - 1) / a.pack : 0);
+    a.ngz = (a.n[1] + kZ - 1) / kZ;
+    a.full_items = a.ngz * a.nty_full * a.ntx;
+    a.per_chunk = a.full_items + (a.remy ? (a.ngz * a.ntx + a.pack - 1) / a.pack : 0);
+    // w chunks of c hyperplanes: an item costs c + 1 steps (one to fill the
+    // state), each CTA runs ceil(items / resident CTAs) items; take the c
+    // with the least of (rounds x steps), the longest any CTA runs.
     const int64_t base = a.per_chunk;
-    const int64_t resident = (int64_t)num_sms * per_sm * kWalk4Warps;
+    const int64_t resident = (int64_t)num_sms * per_sm;
     int64_t best_c = a.n[0], best_cost = -1;
-    // chunk counts k = 1, 2, ... until there are far more items than warps
-    for (int64_t k = 1; k <= a.n[0]; ++k) {
-        const int64_t c = (a.n[0] + k - 1) / k;
+    for (int64_t kc = 1; kc <= a.n[0]; ++kc) {   // chunk counts, until items far outnumber CTAs
+        const int64_t c = (a.n[0] + kc - 1) / kc;
         const int64_t chunks = (a.n[0] + c - 1) / c;
         const int64_t rounds = (chunks * base + resident - 1) / resident;
         const int64_t cost = rounds * (c + 1);
@@ -226,9 +312,8 @@ cudaError_t launch_walk4(Walk4Args a, int num_sms, size_t smem, cudaStream_t s)
     }
     a.chunk = best_c;
     a.items = ((a.n[0] + best_c - 1) / best_c) * base;
-    const int64_t blocks =
-        std::min<int64_t>((a.items + kWalk4Warps - 1) / kWalk4Warps, (int64_t)num_sms * per_sm);
-    k<<<(unsigned)blocks, kWalk4Warps * 32, smem, s>>>(a);
+    const int64_t blocks = std::min<int64_t>(a.items, resident);
+    k<<<(unsigned)blocks, kZ * 32, smem, s>>>(a);
     return cudaGetLastError();
 }
 
@@ -284,12 +369,11 @@ extern "C" ecc_status ecc_compute_nd(ecc_plan_t p, const ecc_image_nd *img, int6
     a.range_check = !(p->d.flags & ECC_FLAG_NO_RANGE_CHECK);
     a.status = p->status;
     a.smem_hist = p->nbins <= kSmemBinsMax;
-    const size_t smem = a.smem_hist ? sizeof(int) * (size_t)p->nbins : 0;
     const bool top = p->d.complex_mode == ECC_TOPCELL_MIN;
-    cudaError_t e = es == 1 ? (top ? launch_walk4<unsigned char, true>(a, p->num_sms, smem, s)
-                                   : launch_walk4<unsigned char, false>(a, p->num_sms, smem, s))
-                            : (top ? launch_walk4<unsigned short, true>(a, p->num_sms, smem, s)
-                                   : launch_walk4<unsigned short, false>(a, p->num_sms, smem, s));
+    cudaError_t e = es == 1 ? (top ? launch_walk4<unsigned char, true>(a, p->num_sms, s)
+                                   : launch_walk4<unsigned char, false>(a, p->num_sms, s))
+                            : (top ? launch_walk4<unsigned short, true>(a, p->num_sms, s)
+                                   : launch_walk4<unsigned short, false>(a, p->num_sms, s));
     p->last_launches = 1;
     if (e == cudaSuccess) {
         e = launch_scan(p->acc, reinterpret_cast<long long *>(d_ecc), reinterpret_cast<long long *>(d_vcec), 1,
