@@ -509,31 +509,40 @@ def run_topcell_and_4d(args):
             ecc.ecc_compute(plan, vol, out)
         kern_ms, kern_n = ecc.ecc_plan_kernel_time(plan)
         res[f"{name}_512cube_stencil_us"] = kern_ms / max(kern_n, 1) * 1e3
-    res["4d"] = []
-    for side, dt, hi in ((64, np.uint8, 255), (128, np.uint8, 255), (64, np.uint16, 1023)):
-        g = torch.Generator(device="cuda")
-        g.manual_seed(6)
-        f = synth.smooth(torch.randn((side,) * 4, generator=g, device="cuda"), 2.0)
-        img4 = synth.quantize(f, dt).contiguous()
-        del f
-        if dt == np.uint16:   # 10-bit levels
-            img4 = (img4.to(torch.int32) // 64).to(torch.uint16)
-        plan = ecc.ecc_plan("u8" if dt == np.uint8 else "u16", 0, hi, max_voxels=img4.numel())
-        out = ecc.ecc_compute_nd(plan, img4)
-        ecc.ecc_status_get(plan)
-        assert int(out[-1].item()) == 1   # the whole box is contractible
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record()
-        for _ in range(5):
-            ecc.ecc_compute_nd(plan, img4, out)
-        b.record()
-        torch.cuda.synchronize()
-        ms = a.elapsed_time(b) / 5
-        res["4d"].append({"workload": f"{side}^4 {np.dtype(dt).name} smoothed field (sigma 2), {hi + 1} bins, "
-                                      "vertex complex",
-                          "ms": ms, "gvox_s": img4.numel() / (ms * 1e-3) / 1e9})
-        del img4
+    res["4d"] = [time_4d(side, dt, hi) for side, dt, hi in ((64, np.uint8, 255), (128, np.uint8, 255),
+                                                             (64, np.uint16, 1023))]
     return res
+
+
+def time_4d(side, dt, hi, reps=5):
+    """One 4D case through ecc_compute_nd: a side^4 smoothed field (sigma 2,
+    seed 6) quantized to dt (uint16: 10-bit levels), vertex complex; mean
+    of `reps` calls timed with CUDA events after one checked call."""
+    import numpy as np
+    import torch
+
+    import paper_2203_09087_gb300 as ecc
+    import synth
+    g = torch.Generator(device="cuda")
+    g.manual_seed(6)
+    f = synth.smooth(torch.randn((side,) * 4, generator=g, device="cuda"), 2.0)
+    img4 = synth.quantize(f, dt).contiguous()
+    del f
+    if dt == np.uint16:   # 10-bit levels
+        img4 = (img4.to(torch.int32) // 64).to(torch.uint16)
+    plan = ecc.ecc_plan("u8" if dt == np.uint8 else "u16", 0, hi, max_voxels=img4.numel())
+    out = ecc.ecc_compute_nd(plan, img4)
+    ecc.ecc_status_get(plan)
+    assert int(out[-1].item()) == 1   # the whole box is contractible
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(reps):
+        ecc.ecc_compute_nd(plan, img4, out)
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / reps
+    return {"workload": f"{side}^4 {np.dtype(dt).name} smoothed field (sigma 2), {hi + 1} bins, vertex complex",
+            "ms": ms, "gvox_s": img4.numel() / (ms * 1e-3) / 1e9}
 
 
 def run_serving(args):
@@ -627,10 +636,16 @@ def main():
                     help="duration of the Poisson request stream in --extras (configuration: 60)")
     ap.add_argument("--quick", action="store_true",
                     help="profiler runs: no one-second warm-up floor, no e2e and CPU legs")
+    ap.add_argument("--only-4d", type=int, default=0, metavar="SIDE",
+                    help="profiler runs: only the 4D case SIDE^4 uint8 (three calls after the checked one)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     if args.impl == "reference":
         return run_reference(args)
+    if args.only_4d:
+        import numpy as np
+        print(json.dumps(time_4d(args.only_4d, np.uint8, 255, reps=3)))
+        return
 
     import numpy as np
     import torch

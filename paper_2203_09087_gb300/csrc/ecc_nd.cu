@@ -44,9 +44,13 @@ namespace {
 // halves it does not need itself go through shared memory to the warps of
 // z-1 and z+1, which read them at the next step (one __syncthreads a step;
 // slices triple-buffered, exchanged wins double-buffered, by step).  The
-// halo pairs are spread over warps 1 and 2; warps 0 and kZ-1 load the halo
-// slices.
-constexpr int kZ = 4;
+// three halo pairs go to warps 1-3 (1 and 2 when kZ = 4); warps 0 and kZ-1
+// load the halo slices.  kZ = 4 for 8-bit images (4 and 6 measured alike,
+// 8 slower); 16-bit ones, at about 230 registers a thread, fit 8 warps per
+// SM either way and take kZ = 8 (fewer halo loads and pairs per output:
+// 209 against 245 us at 64^4).
+template <typename T>
+__host__ __device__ constexpr int z_group() { return sizeof(T) == 1 ? 4 : 8; }
 
 struct Walk4Args {
     const unsigned char *data;
@@ -56,7 +60,7 @@ struct Walk4Args {
     int64_t chunk;       // hyperplanes per item
     int64_t per_chunk;   // items per w chunk: full_items, then the packed ones
     int64_t full_items;  // z groups x full row tiles x windows
-    int64_t ngz;         // groups of kZ consecutive z
+    int64_t ngz;         // groups of z_group<T>() consecutive z
     int32_t ntx;         // windows of 30 columns
     int32_t nty_full;    // tiles of 30 rows
     int32_t remy;        // rows left below the full tiles (0..29)
@@ -68,20 +72,23 @@ struct Walk4Args {
 
 // Shared-memory words before the histogram: slices of three hyperplanes
 // (kZ + 2 each, KP planes) and three double-buffered win exchanges.
-__host__ __device__ constexpr int walk4_slice_words(int KP) { return 3 * (kZ + 2) * KP * 32; }
-__host__ __device__ constexpr int walk4_xchg_words() { return 2 * kZ * 9 * 32; }
-__host__ __device__ constexpr int walk4_words(int KP) { return walk4_slice_words(KP) + 3 * walk4_xchg_words(); }
+__host__ __device__ constexpr int walk4_slice_words(int kZ, int KP) { return 3 * (kZ + 2) * KP * 32; }
+__host__ __device__ constexpr int walk4_xchg_words(int kZ) { return 2 * kZ * 9 * 32; }
+__host__ __device__ constexpr int walk4_words(int kZ, int KP)
+{
+    return walk4_slice_words(kZ, KP) + 3 * walk4_xchg_words(kZ);
+}
 
 template <typename T, bool TOP>
-__global__ void __launch_bounds__(kZ * 32) walk4d_kernel(const Walk4Args a)
+__global__ void __launch_bounds__(z_group<T>() * 32) walk4d_kernel(const Walk4Args a)
 {
-    constexpr int K = 8 * sizeof(T), KP = K + 1;
+    constexpr int K = 8 * sizeof(T), KP = K + 1, kZ = z_group<T>();
     extern __shared__ uint32_t smem4[];
     uint32_t *const SL = smem4;                                   // [3][kZ + 2][KP][32]
-    uint32_t *const MZ = SL + walk4_slice_words(KP);              // [2][kZ][9][32]
-    uint32_t *const CM = MZ + walk4_xchg_words();
-    uint32_t *const CP = CM + walk4_xchg_words();
-    int *const hist = reinterpret_cast<int *>(CP + walk4_xchg_words());
+    uint32_t *const MZ = SL + walk4_slice_words(kZ, KP);          // [2][kZ][9][32]
+    uint32_t *const CM = MZ + walk4_xchg_words(kZ);
+    uint32_t *const CP = CM + walk4_xchg_words(kZ);
+    int *const hist = reinterpret_cast<int *>(CP + walk4_xchg_words(kZ));
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     if (a.smem_hist)
         for (int i = threadIdx.x; i < a.h.nbins; i += blockDim.x) hist[i] = 0;
@@ -228,7 +235,7 @@ __global__ void __launch_bounds__(kZ * 32) walk4d_kernel(const Walk4Args a)
                 walk::slice_pair<K, TOP, true, true>(B0, Bp, W2, rv);
                 if (warp < kZ - 1) put9(xchg(MZ, par, warp + 1), rv);
             }
-            // the halo pairs of warps 0 and kZ-1
+            // the halo pairs of warps 0 and kZ-1 (kZ = 4: warp 2 takes two)
             if (warp == 1) {
                 uint32_t X[KP], Y[KP];
                 get_slice(hB, 0, X);
@@ -241,6 +248,9 @@ __global__ void __launch_bounds__(kZ * 32) walk4d_kernel(const Walk4Args a)
                 get_slice(hB, 1, Y);
                 walk::slice_pair<K, TOP, false, true>(X, Y, fw, rv);
                 put9(xchg(CM, par, 0), rv);
+            }
+            if (warp == (kZ > 4 ? 3 : 2)) {
+                uint32_t X[KP], Y[KP];
                 get_slice(hA, kZ + 1, X);
                 get_slice(hB, kZ, Y);
                 walk::slice_pair<K, TOP, false, true>(X, Y, fw, rv);
@@ -275,9 +285,10 @@ __global__ void __launch_bounds__(kZ * 32) walk4d_kernel(const Walk4Args a)
 template <typename T, bool TOP>
 cudaError_t launch_walk4(Walk4Args a, int num_sms, cudaStream_t s)
 {
-    constexpr int KP = 8 * sizeof(T) + 1;
+    constexpr int KP = 8 * sizeof(T) + 1, kZ = z_group<T>();
     auto k = walk4d_kernel<T, TOP>;
-    const size_t smem = sizeof(uint32_t) * (size_t)walk4_words(KP) + (a.smem_hist ? sizeof(int) * (size_t)a.h.nbins : 0);
+    const size_t smem =
+        sizeof(uint32_t) * (size_t)walk4_words(kZ, KP) + (a.smem_hist ? sizeof(int) * (size_t)a.h.nbins : 0);
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
