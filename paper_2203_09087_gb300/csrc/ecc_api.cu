@@ -268,6 +268,10 @@ ecc_status ecc_status_get(ecc_plan_t p, void *stream)
         set_error("an image value lies outside [lo, hi]");
         return ECC_E_RANGE;
     }
+    if (word & DEV_STATE) {
+        set_error("the scan's look-back state was not clean (plan workspace corrupted)");
+        return ECC_E_CUDA;
+    }
     if (word & DEV_LEVELS) {
         set_error("the threshold levels are not in ascending order");
         return ECC_E_INVALID;

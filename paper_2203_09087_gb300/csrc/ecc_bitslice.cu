@@ -208,8 +208,9 @@ __global__ void __launch_bounds__((NW + 1) * 32, bs3d_min_blocks<T, NW>())
             int64_t g = 0;
             bool live = true;
             while (live) {
-                const int item = (int)atomicAdd(a.sched, 1u);
-                const bool more = item < a.nitems;
+                const unsigned int claimed = atomicAdd(a.sched, 1u);
+                const bool more = claimed < (unsigned int)a.nitems;   // unsigned: never a negative item
+                const int item = more ? (int)claimed : 0;
                 int xt = 0, yt = 0;
                 int64_t zb = 0, ze = -1;
                 if (more) decode(item, xt, yt, zb, ze);

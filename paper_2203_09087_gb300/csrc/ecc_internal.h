@@ -16,6 +16,7 @@ enum : uint32_t {
     DEV_RANGE = 1u,    // an image value outside [lo, hi]
     DEV_TIMEOUT = 2u,  // a bounded spin-wait gave up
     DEV_LEVELS = 4u,   // threshold levels not in ascending order
+    DEV_STATE = 8u,    // a scan tile claimed an index past its grid (look-back state not clean)
 };
 
 // Upper bound for every device-side spin-wait (nanoseconds of %globaltimer).
@@ -99,6 +100,12 @@ cudaError_t launch_scan(unsigned long long *acc, long long *ecc, long long *vcec
                         int32_t nbins, const ScanWs &ws, unsigned int *status, cudaStream_t s);
 
 int64_t scan_tiles(int64_t n_seg, int32_t nbins);
+
+// Zeroes device memory and returns once the zeros are in place (a private
+// non-blocking stream, synchronized).  A plain cudaMemset runs on the legacy
+// default stream, which work launched later on a non-blocking stream does
+// not wait for: that launch could run first and have its results cleared.
+cudaError_t clear_device_now(void *p, size_t bytes);
 
 // --------------------------------------------------------------- errors
 

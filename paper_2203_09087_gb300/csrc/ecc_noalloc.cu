@@ -65,7 +65,7 @@ ecc_status scratch_for_current_device(unsigned long long **out)
         void *p = nullptr;
         e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess) return cuda_fail(e, "ecc_compute_noalloc: cudaGetSymbolAddress");
-        e = cudaMemset(p, 0, sizeof(g_noalloc_scratch));
+        e = clear_device_now(p, sizeof(g_noalloc_scratch));
         if (e != cudaSuccess) return cuda_fail(e, "ecc_compute_noalloc: scratch clear");
         g_ptr[dev] = static_cast<unsigned long long *>(p);
     }
@@ -143,6 +143,10 @@ extern "C" ecc_status ecc_compute_noalloc(const ecc_image *img, int32_t lo, int3
     if (word & DEV_TIMEOUT) {
         set_error("a bounded device-side wait gave up");
         return ECC_E_TIMEOUT;
+    }
+    if (word & DEV_STATE) {
+        set_error("the scan's look-back state was not clean (scratch corrupted)");
+        return ECC_E_CUDA;
     }
     if (word & DEV_RANGE) {
         set_error("an image value lies outside [lo, hi]");

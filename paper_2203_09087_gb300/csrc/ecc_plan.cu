@@ -9,6 +9,16 @@ using namespace ecc;
 
 static size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
+cudaError_t ecc::clear_device_now(void *p, size_t bytes)
+{
+    cudaStream_t s = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMemsetAsync(p, 0, bytes, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (s) cudaStreamDestroy(s);
+    return e;
+}
+
 ecc_status ecc_plan_s::allocate()
 {
     const int64_t max_seg = d.max_images;
@@ -26,7 +36,9 @@ ecc_status ecc_plan_s::allocate()
         set_error("ecc_plan: cudaMalloc of the workspace failed");
         return ECC_E_NOMEM;
     }
-    e = cudaMemset(ws, 0, ws_bytes);
+    // the histogram, status and scan workspace start at zero before any
+    // stream, the caller's non-blocking ones included, can use them
+    e = clear_device_now(ws, ws_bytes);
     if (e != cudaSuccess) return cuda_fail(e, "ecc_plan: workspace clear");
     unsigned char *b = static_cast<unsigned char *>(ws);
     acc = reinterpret_cast<unsigned long long *>(b);

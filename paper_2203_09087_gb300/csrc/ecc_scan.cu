@@ -38,6 +38,13 @@ __global__ void __launch_bounds__(kScanThreads) scan_kernel(ScanArgs a)
     if (threadIdx.x == 0) s_tile = atomicAdd(a.ws.tile_counter, 1u);
     __syncthreads();
     const int64_t tile = s_tile;
+    // The counter starts at zero (plan creation, and every scan's last tile
+    // resets it), so the index is below the grid; if the state was ever not
+    // clean, report it and touch nothing rather than write past the arrays.
+    if (tile >= (int64_t)gridDim.x) {
+        if (threadIdx.x == 0) atomicOr(a.status, DEV_STATE);
+        return;
+    }
     const int64_t base = tile * kScanTile + (int64_t)threadIdx.x * kScanItems;
 
     long long v[kScanItems], orig[kScanItems];
