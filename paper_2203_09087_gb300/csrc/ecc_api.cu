@@ -84,11 +84,12 @@ ecc_status image_geom(const ecc_image *img, int32_t want_dtype, int64_t max_voxe
 // Launch the stencil+histogram pass of one image over outer indices
 // [ob, oe) into the histogram h.
 static cudaError_t launch_stencil_untimed(ecc_plan_s *p, const Geom &g, int64_t ob, int64_t oe, const HistDst &h,
-                                         cudaStream_t s);
+                                         cudaStream_t s, FusedScan *fs);
 
-cudaError_t launch_stencil(ecc_plan_s *p, const Geom &g, int64_t ob, int64_t oe, const HistDst &h, cudaStream_t s)
+cudaError_t launch_stencil(ecc_plan_s *p, const Geom &g, int64_t ob, int64_t oe, const HistDst &h, cudaStream_t s,
+                           FusedScan *fs)
 {
-    if (!(p->d.flags & ECC_FLAG_TIME_KERNELS)) return launch_stencil_untimed(p, g, ob, oe, h, s);
+    if (!(p->d.flags & ECC_FLAG_TIME_KERNELS)) return launch_stencil_untimed(p, g, ob, oe, h, s, fs);
     while (p->time_ev.size() < p->time_used + 2) {
         cudaEvent_t ev;
         cudaError_t e = cudaEventCreate(&ev);
@@ -98,20 +99,20 @@ cudaError_t launch_stencil(ecc_plan_s *p, const Geom &g, int64_t ob, int64_t oe,
     cudaEvent_t t0 = p->time_ev[p->time_used], t1 = p->time_ev[p->time_used + 1];
     p->time_used += 2;
     cudaError_t e = cudaEventRecord(t0, s);
-    if (e == cudaSuccess) e = launch_stencil_untimed(p, g, ob, oe, h, s);
+    if (e == cudaSuccess) e = launch_stencil_untimed(p, g, ob, oe, h, s, fs);
     if (e == cudaSuccess) e = cudaEventRecord(t1, s);
     return e;
 }
 
 static cudaError_t launch_stencil_untimed(ecc_plan_s *p, const Geom &g, int64_t ob, int64_t oe, const HistDst &h,
-                                         cudaStream_t s)
+                                         cudaStream_t s, FusedScan *fs)
 {
     const bool range = !(p->d.flags & ECC_FLAG_NO_RANGE_CHECK);
     const bool want_bitslice = !(p->d.flags & ECC_FLAG_KERNEL_DIRECT);
     if (want_bitslice && bitslice_supported(g)) {
         const int tp = p->tune_param(g);
         cudaError_t e =
-            launch_bitslice(g, ob, oe, h, p->d.complex_mode, range, p->status, p->sched, p->num_sms, tp, s);
+            launch_bitslice(g, ob, oe, h, p->d.complex_mode, range, p->status, p->sched, p->num_sms, tp, s, fs);
         if (e != cudaErrorNotSupported) {
             ++p->last_launches;
             return e;
@@ -239,8 +240,11 @@ ecc_status ecc_compute(ecc_plan_t p, const ecc_image *img, int64_t *d_ecc, int64
     HistDst h{p->acc, p->d.lo, p->nbins};
     if (p->d.flags & ECC_FLAG_COUNT_EMITTED) h.emitted = p->emitted;
     const int64_t outer = g.ndim == 3 ? g.nz : g.ny;
-    cudaError_t e = launch_stencil(p, g, 0, outer, h, s);
+    // the 3D stencil's last CTA scans small histograms itself (fs.done)
+    FusedScan fs{reinterpret_cast<long long *>(d_ecc), reinterpret_cast<long long *>(d_vcec), false};
+    cudaError_t e = launch_stencil(p, g, 0, outer, h, s, &fs);
     if (e != cudaSuccess) return cuda_fail(e, "ecc_compute: stencil launch");
+    if (fs.done) return ECC_OK;
     e = launch_scan(p->acc, reinterpret_cast<long long *>(d_ecc), reinterpret_cast<long long *>(d_vcec), 1,
                     p->nbins, p->scan_ws(), p->status, s);
     ++p->last_launches;

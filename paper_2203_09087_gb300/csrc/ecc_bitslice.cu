@@ -78,7 +78,43 @@ struct Bs3dArgs {
     int32_t range_check;
     HistDst h;
     unsigned int *status;
+    long long *ecc_out;      // non-null: the last CTA also scans the bins (whole image, small histogram)
+    long long *vcec_out;
 };
+
+// Inclusive scan of the accumulated bins by one CTA of NTH threads, the
+// fused form of the scan kernel for small histograms (Sec. 2.3: the ECC is
+// the prefix sum of the VCEC): ecc[i] = acc[0] + ... + acc[i], vcec[i] =
+// acc[i] if asked, and acc is left zero for the next call.  Each thread takes
+// a contiguous run of bins; the runs' sums are scanned across the CTA.
+template <int NTH>
+__device__ void scan_bins(unsigned long long *acc, long long *ecc, long long *vcec, int nbins, int tid)
+{
+    __shared__ long long s_warp[NTH / 32];
+    const int lane = tid & 31, warp = tid >> 5;
+    const int per = (nbins + NTH - 1) / NTH;
+    const int b0 = tid * per < nbins ? tid * per : nbins;
+    const int b1 = b0 + per < nbins ? b0 + per : nbins;
+    long long sum = 0;
+    for (int i = b0; i < b1; ++i) sum += (long long)__ldcg(acc + i);
+    long long x = sum;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const long long y = __shfl_up_sync(0xffffffffu, x, off);
+        if (lane >= off) x += y;
+    }
+    if (lane == 31) s_warp[warp] = x;
+    __syncthreads();
+    long long run = x - sum;   // this thread's exclusive prefix
+    for (int w = 0; w < warp; ++w) run += s_warp[w];
+    for (int i = b0; i < b1; ++i) {
+        const long long v = (long long)__ldcg(acc + i);
+        run += v;
+        ecc[i] = run;
+        if (vcec) vcec[i] = v;
+        acc[i] = 0ull;
+    }
+}
 
 // ----------------------------------------------------------------- TMA
 
@@ -363,7 +399,11 @@ __global__ void __launch_bounds__((NW + 1) * 32, bs3d_min_blocks<T, NW>())
             for (int r = 0; r < HREP; ++r) v += hist[r * a.h.nbins + i];
             if (v) atomicAdd(a.h.acc + i, (unsigned long long)(long long)v);
         }
-    // the last CTA resets the item counter for the next launch
+    // The last CTA to finish resets the item counter for the next launch and,
+    // when asked, scans the bins: the CTA's adds to acc (ordered before thread
+    // 0 by the barrier) are made visible device-wide by its fence before the
+    // CTA counts itself finished.
+    __syncthreads();
     if (tid == 0) {
         __threadfence();
         s_last = atomicAdd(a.sched + 1, 1u) == gridDim.x - 1;
@@ -372,6 +412,10 @@ __global__ void __launch_bounds__((NW + 1) * 32, bs3d_min_blocks<T, NW>())
             a.sched[1] = 0u;
             __threadfence();
         }
+    }
+    if (a.ecc_out) {
+        __syncthreads();
+        if (s_last) scan_bins<NTH>(a.h.acc, a.ecc_out, a.vcec_out, a.h.nbins, tid);
     }
 }
 
@@ -544,7 +588,7 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
 
 template <typename T, int NW, bool TOP, int HREP>
 cudaError_t launch_t(const Geom &g, int64_t zb, int64_t ze, const HistDst &h, bool range_check,
-                     unsigned int *status, unsigned int *sched, int num_sms, cudaStream_t s)
+                     unsigned int *status, unsigned int *sched, int num_sms, cudaStream_t s, FusedScan *fs)
 {
     using C = Cfg<T>;
     constexpr int BWB = box_bytes(NW, C::ES);
@@ -573,6 +617,9 @@ cudaError_t launch_t(const Geom &g, int64_t zb, int64_t ze, const HistDst &h, bo
     a.h = h;
     a.range_check = range_check;
     a.status = status;
+    const bool fuse = fs && fs->ecc && zb == 0 && ze == g.nz && h.nbins <= kFusedScanMaxBins;
+    a.ecc_out = fuse ? fs->ecc : nullptr;
+    a.vcec_out = fuse ? fs->vcec : nullptr;
     const size_t stage_bytes = (size_t)C::S * 32 * BWB + (size_t)C::S * 16;
     a.smem_hist = (size_t)HREP * h.nbins * 4 + stage_bytes <= 160 * 1024;
     const size_t smem = stage_bytes + (a.smem_hist ? (size_t)HREP * h.nbins * 4 : 0);
@@ -633,19 +680,21 @@ cudaError_t launch_t(const Geom &g, int64_t zb, int64_t ze, const HistDst &h, bo
     a.nitems = (int32_t)items;
     const int64_t ctas = items < ctas_max ? items : ctas_max;
     kern<<<(unsigned)ctas, (NW + 1) * 32, smem, s>>>(map, a);
-    return cudaGetLastError();
+    const cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess && fuse) fs->done = true;
+    return e;
 }
 
 template <int NW, int HREP>
 cudaError_t launch_nw(const Geom &g, int64_t zb, int64_t ze, const HistDst &h, int mode, bool rc, unsigned int *st,
-                      unsigned int *sched, int sms, cudaStream_t s)
+                      unsigned int *sched, int sms, cudaStream_t s, FusedScan *fs)
 {
     const bool top = mode == ECC_TOPCELL_MIN;
     if (g.esize == 1)
-        return top ? launch_t<unsigned char, NW, true, HREP>(g, zb, ze, h, rc, st, sched, sms, s)
-                   : launch_t<unsigned char, NW, false, HREP>(g, zb, ze, h, rc, st, sched, sms, s);
-    return top ? launch_t<unsigned short, NW, true, HREP>(g, zb, ze, h, rc, st, sched, sms, s)
-               : launch_t<unsigned short, NW, false, HREP>(g, zb, ze, h, rc, st, sched, sms, s);
+        return top ? launch_t<unsigned char, NW, true, HREP>(g, zb, ze, h, rc, st, sched, sms, s, fs)
+                   : launch_t<unsigned char, NW, false, HREP>(g, zb, ze, h, rc, st, sched, sms, s, fs);
+    return top ? launch_t<unsigned short, NW, true, HREP>(g, zb, ze, h, rc, st, sched, sms, s, fs)
+               : launch_t<unsigned short, NW, false, HREP>(g, zb, ze, h, rc, st, sched, sms, s, fs);
 }
 
 }  // namespace
@@ -665,7 +714,7 @@ bool bitslice_supported(const Geom &g)
 // + (shared histogram copies): 61, 62, 42, 31 (the autotuner's candidates).
 cudaError_t launch_bitslice(const Geom &g, int64_t outer_begin, int64_t outer_end, const HistDst &h, int mode,
                             bool range_check, unsigned int *status, unsigned int *sched, int num_sms, int tune_param,
-                            cudaStream_t s)
+                            cudaStream_t s, FusedScan *fs)
 {
     if (outer_end <= outer_begin) return cudaSuccess;
     if (!bitslice_supported(g)) return cudaErrorNotSupported;
@@ -691,10 +740,10 @@ cudaError_t launch_bitslice(const Geom &g, int64_t outer_begin, int64_t outer_en
         }
     }
     switch (tp) {
-    case 61: return launch_nw<6, 1>(g, outer_begin, outer_end, h, mode, range_check, status, sched, num_sms, s);
-    case 62: return launch_nw<6, 2>(g, outer_begin, outer_end, h, mode, range_check, status, sched, num_sms, s);
-    case 42: return launch_nw<4, 2>(g, outer_begin, outer_end, h, mode, range_check, status, sched, num_sms, s);
-    default: return launch_nw<3, 1>(g, outer_begin, outer_end, h, mode, range_check, status, sched, num_sms, s);
+    case 61: return launch_nw<6, 1>(g, outer_begin, outer_end, h, mode, range_check, status, sched, num_sms, s, fs);
+    case 62: return launch_nw<6, 2>(g, outer_begin, outer_end, h, mode, range_check, status, sched, num_sms, s, fs);
+    case 42: return launch_nw<4, 2>(g, outer_begin, outer_end, h, mode, range_check, status, sched, num_sms, s, fs);
+    default: return launch_nw<3, 1>(g, outer_begin, outer_end, h, mode, range_check, status, sched, num_sms, s, fs);
     }
 }
 

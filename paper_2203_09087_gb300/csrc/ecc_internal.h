@@ -84,6 +84,16 @@ cudaError_t launch_direct(const Geom &g, int64_t outer_begin, int64_t outer_end,
                           int complex_mode, bool range_check, unsigned int *status,
                           int num_sms, cudaStream_t s);
 
+// A stencil launch over a whole image may also do the scan in its last CTA
+// when the histogram is small (no second launch): where the ECC (and VCEC,
+// if not null) go; `done` is set when the launch took the scan on.
+struct FusedScan {
+    long long *ecc = nullptr;
+    long long *vcec = nullptr;
+    bool done = false;
+};
+constexpr int kFusedScanMaxBins = 4096;
+
 // Bit-sliced stencil + histogram (3D and 2D, uint8 / uint16, both complexes).
 // Returns cudaErrorNotSupported when the geometry does not qualify.
 bool bitslice_supported(const Geom &g);
@@ -91,7 +101,7 @@ bool bitslice_supported(const Geom &g);
 // them zero again (its dynamic item counter and finished-CTA count).
 cudaError_t launch_bitslice(const Geom &g, int64_t outer_begin, int64_t outer_end, const HistDst &h,
                             int complex_mode, bool range_check, unsigned int *status, unsigned int *sched,
-                            int num_sms, int tune_param, cudaStream_t s);
+                            int num_sms, int tune_param, cudaStream_t s, FusedScan *fs = nullptr);
 
 // Segmented inclusive scan of n_seg * nbins int64 values (segment i =
 // elements [i*nbins, (i+1)*nbins)).  Reads acc, writes ecc (and vcec if not

@@ -86,7 +86,7 @@ namespace ecc {
 ecc_status image_geom(const ecc_image *img, int32_t want_dtype, int64_t max_voxels, Geom *g, int64_t *voxels,
                       bool allow_null_data);
 cudaError_t launch_stencil(ecc_plan_s *p, const Geom &g, int64_t ob, int64_t oe, const HistDst &h,
-                           cudaStream_t s);
+                           cudaStream_t s, FusedScan *fs = nullptr);
 void release_batch(ecc_plan_s *p);
 cudaError_t launch_batch_single(ecc_plan_s *p, const Geom &g, const HistDst &h, cudaStream_t s);
 

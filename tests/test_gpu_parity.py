@@ -131,6 +131,36 @@ def test_subrange_and_vcec_output(mode):
 
 
 @pytest.mark.parametrize("mode", list(MODES))
+def test_fused_scan_in_the_3d_stencil(mode):
+    """The 3D stencil's last CTA scans histograms of up to 4096 bins itself
+    (no scan launch).  ECC and VCEC equal the oracle's on both sides of that
+    limit (4096 bins fused, 4097 and 65536 through the scan kernel), for
+    volumes whose rows the TMA addresses and that span many CTAs, over
+    repeated calls on one plan (the accumulator and the CTA counter are left
+    clean for the next call)."""
+    ecc = ecc_mod()
+    rng = np.random.default_rng(17)
+    img8 = rng.integers(0, 256, size=(37, 61, 96), dtype=np.uint8)
+    img16 = rng.integers(0, 4096, size=(29, 70, 128), dtype=np.uint16)
+    for img, lo, hi in ((img8, 0, 255), (img8, 0, 199), (img16, 0, 4095), (img16, 0, 4096), (img16, 0, 65535)):
+        if img.max() > hi:
+            img = np.minimum(img, hi).astype(img.dtype)
+        t = _gpu(img)
+        dt = "u8" if img.dtype == np.uint8 else "u16"
+        plan = ecc.ecc_plan(dt, lo, hi, complex_mode=MODES[mode], max_voxels=img.size)
+        want_e, want_v = _expect(img, lo, hi, mode), oracle.vcec(img, lo, hi, mode)
+        for _ in range(3):
+            out = torch.full((hi - lo + 1,), -777, dtype=torch.int64, device="cuda")
+            v = torch.full((hi - lo + 1,), -777, dtype=torch.int64, device="cuda")
+            ecc.ecc_compute(plan, t, out, v)
+            ecc.ecc_status_get(plan)
+            assert np.array_equal(out.cpu().numpy(), want_e), (img.dtype, hi)
+            assert np.array_equal(v.cpu().numpy(), want_v), (img.dtype, hi)
+        assert ecc.ecc_plan_last_launches(plan) == (1 if hi - lo + 1 <= 4096 else 2)
+        plan.close()
+
+
+@pytest.mark.parametrize("mode", list(MODES))
 @pytest.mark.parametrize("kernel", list(KERNELS))
 def test_pitched_views(mode, kernel):
     rng = np.random.default_rng(4)
