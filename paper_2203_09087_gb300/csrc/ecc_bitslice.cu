@@ -439,6 +439,9 @@ struct Bs2dArgs {
     int32_t smem_hist, range_check;
     HistDst h;
     unsigned int *status;
+    long long *ecc_out;      // non-null: the last CTA also scans the bins (whole image, small histogram)
+    long long *vcec_out;
+    unsigned int *done;      // finished-CTA count for the fused scan (zero between launches)
 };
 
 constexpr int kWarps2d = 4;
@@ -509,14 +512,33 @@ __global__ void __launch_bounds__(kWarps2d * 32, 4) bs2d_kernel(const Bs2dArgs a
             for (int r = 0; r < HREP; ++r) v += hist2[r * a.h.nbins + i];
             if (v) atomicAdd(a.h.acc + i, (unsigned long long)(long long)v);
         }
+    if (a.ecc_out) {
+        // the last CTA to finish scans the bins (as the 3D kernel does)
+        __shared__ int s_last2;
+        __syncthreads();
+        if (tid == 0) {
+            __threadfence();
+            s_last2 = atomicAdd(a.done, 1u) == gridDim.x - 1;
+            if (s_last2) {
+                *a.done = 0u;
+                __threadfence();
+            }
+        }
+        __syncthreads();
+        if (s_last2) scan_bins<kWarps2d * 32>(a.h.acc, a.ecc_out, a.vcec_out, a.h.nbins, tid);
+    }
 }
 
 template <typename T, bool TOP>
 cudaError_t launch_2d_t(const Geom &g, int64_t yb, int64_t ye, const HistDst &h, bool range_check,
-                        unsigned int *status, int num_sms, cudaStream_t s)
+                        unsigned int *status, int num_sms, cudaStream_t s, unsigned int *done, FusedScan *fs)
 {
     constexpr int HREP = 2;
     Bs2dArgs a{};
+    const bool fuse = fs && fs->ecc && done && yb == 0 && ye == g.ny && h.nbins <= kFusedScanMaxBins;
+    a.ecc_out = fuse ? fs->ecc : nullptr;
+    a.vcec_out = fuse ? fs->vcec : nullptr;
+    a.done = done;
     a.data = g.data;
     a.nx = g.nx;
     a.ny = g.ny;
@@ -566,7 +588,9 @@ cudaError_t launch_2d_t(const Geom &g, int64_t yb, int64_t ye, const HistDst &h,
     const int64_t ctas_max = (int64_t)num_sms * per_sm_cached;
     if (ctas > ctas_max) ctas = ctas_max;
     kern<<<(unsigned)ctas, kWarps2d * 32, smem, s>>>(a);
-    return cudaGetLastError();
+    const cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess && fuse) fs->done = true;
+    return e;
 }
 
 // ----------------------------------------------------------------- host side
@@ -720,11 +744,18 @@ cudaError_t launch_bitslice(const Geom &g, int64_t outer_begin, int64_t outer_en
     if (!bitslice_supported(g)) return cudaErrorNotSupported;
     if (g.ndim == 2) {
         const bool top = mode == ECC_TOPCELL_MIN;
+        // the fused scan's finished-CTA count: a word of the scheduling block
+        // the 3D kernel does not use
+        unsigned int *done = sched ? sched + 2 : nullptr;
         if (g.esize == 1)
-            return top ? launch_2d_t<unsigned char, true>(g, outer_begin, outer_end, h, range_check, status, num_sms, s)
-                       : launch_2d_t<unsigned char, false>(g, outer_begin, outer_end, h, range_check, status, num_sms, s);
-        return top ? launch_2d_t<unsigned short, true>(g, outer_begin, outer_end, h, range_check, status, num_sms, s)
-                   : launch_2d_t<unsigned short, false>(g, outer_begin, outer_end, h, range_check, status, num_sms, s);
+            return top ? launch_2d_t<unsigned char, true>(g, outer_begin, outer_end, h, range_check, status, num_sms,
+                                                          s, done, fs)
+                       : launch_2d_t<unsigned char, false>(g, outer_begin, outer_end, h, range_check, status, num_sms,
+                                                           s, done, fs);
+        return top ? launch_2d_t<unsigned short, true>(g, outer_begin, outer_end, h, range_check, status, num_sms, s,
+                                                       done, fs)
+                   : launch_2d_t<unsigned short, false>(g, outer_begin, outer_end, h, range_check, status, num_sms,
+                                                        s, done, fs);
     }
     int tp = tune_param;
     if (tp != 61 && tp != 62 && tp != 42 && tp != 31) {

@@ -131,18 +131,21 @@ def test_subrange_and_vcec_output(mode):
 
 
 @pytest.mark.parametrize("mode", list(MODES))
-def test_fused_scan_in_the_3d_stencil(mode):
-    """The 3D stencil's last CTA scans histograms of up to 4096 bins itself
-    (no scan launch).  ECC and VCEC equal the oracle's on both sides of that
-    limit (4096 bins fused, 4097 and 65536 through the scan kernel), for
-    volumes whose rows the TMA addresses and that span many CTAs, over
-    repeated calls on one plan (the accumulator and the CTA counter are left
-    clean for the next call)."""
+def test_fused_scan_in_the_stencils(mode):
+    """The 3D and 2D stencils' last CTA scans histograms of up to 4096 bins
+    itself (no scan launch).  ECC and VCEC equal the oracle's on both sides
+    of that limit (4096 bins fused, 4097 and 65536 through the scan kernel),
+    for 3D volumes whose rows the TMA addresses and 2D images, spanning many
+    CTAs, over repeated calls on one plan (the accumulator and the CTA
+    counters are left clean for the next call)."""
     ecc = ecc_mod()
     rng = np.random.default_rng(17)
     img8 = rng.integers(0, 256, size=(37, 61, 96), dtype=np.uint8)
     img16 = rng.integers(0, 4096, size=(29, 70, 128), dtype=np.uint16)
-    for img, lo, hi in ((img8, 0, 255), (img8, 0, 199), (img16, 0, 4095), (img16, 0, 4096), (img16, 0, 65535)):
+    img2 = rng.integers(0, 256, size=(700, 1333), dtype=np.uint8)
+    img2w = rng.integers(0, 4096, size=(301, 2900), dtype=np.uint16)
+    for img, lo, hi in ((img8, 0, 255), (img8, 0, 199), (img16, 0, 4095), (img16, 0, 4096), (img16, 0, 65535),
+                        (img2, 0, 255), (img2w, 0, 4095), (img2w, 0, 4096)):
         if img.max() > hi:
             img = np.minimum(img, hi).astype(img.dtype)
         t = _gpu(img)
