@@ -63,7 +63,8 @@ def _traffic_for(kernel_digest: str):
     return ent.get("dram_bytes_per_launch")
 
 
-STENCIL_SOURCES = ("ecc_bitslice.cu", "ecc_bitslice.cuh", "ecc_walk.cuh", "ecc_sync.cuh", "ecc_internal.h")
+STENCIL_SOURCES = ("ecc_bitslice.cu", "ecc_bitslice.cuh", "ecc_walk.cuh", "ecc_sync.cuh", "ecc_internal.h",
+                   "ecc_scan_block.cuh")
 
 
 def _kernel_digest():

@@ -20,6 +20,7 @@
 #include "ecc_bitslice.cuh"
 #include "ecc_internal.h"
 #include "ecc_plan.h"
+#include "ecc_scan_block.cuh"
 #include "ecc_walk.cuh"
 
 namespace ecc {
@@ -68,6 +69,9 @@ struct Walk4Args {
     HistDst h;
     int32_t smem_hist, range_check;
     unsigned int *status;
+    long long *ecc_out;    // non-null: the last CTA also scans the bins (at most kFusedScanMaxBins)
+    long long *vcec_out;
+    unsigned int *done;    // finished-CTA count for that scan (zero between launches)
 };
 
 // Shared-memory words before the histogram: slices of three hyperplanes
@@ -280,11 +284,29 @@ __global__ void __launch_bounds__(z_group<T>() * 32) walk4d_kernel(const Walk4Ar
     if (a.smem_hist)
         for (int i = threadIdx.x; i < a.h.nbins; i += blockDim.x)
             if (hist[i]) atomicAdd(a.h.acc + i, (unsigned long long)(long long)hist[i]);
+    if (a.ecc_out) {
+        // the last CTA to finish scans the bins (as the 2D and 3D stencils do)
+        __shared__ int s_last;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            __threadfence();
+            s_last = atomicAdd(a.done, 1u) == gridDim.x - 1;
+            if (s_last) {
+                *a.done = 0u;
+                __threadfence();
+            }
+        }
+        __syncthreads();
+        if (s_last) scan_bins<kZ * 32>(a.h.acc, a.ecc_out, a.vcec_out, a.h.nbins, threadIdx.x);
+    }
 }
 
 template <typename T, bool TOP>
-cudaError_t launch_walk4(Walk4Args a, int num_sms, cudaStream_t s)
+cudaError_t launch_walk4(Walk4Args a, int num_sms, cudaStream_t s, FusedScan *fs)
 {
+    const bool fuse = fs && fs->ecc && a.done && a.h.nbins <= kFusedScanMaxBins;
+    a.ecc_out = fuse ? fs->ecc : nullptr;
+    a.vcec_out = fuse ? fs->vcec : nullptr;
     constexpr int KP = 8 * sizeof(T) + 1, kZ = z_group<T>();
     auto k = walk4d_kernel<T, TOP>;
     const size_t smem =
@@ -325,7 +347,9 @@ cudaError_t launch_walk4(Walk4Args a, int num_sms, cudaStream_t s)
     a.items = ((a.n[0] + best_c - 1) / best_c) * base;
     const int64_t blocks = std::min<int64_t>(a.items, resident);
     k<<<(unsigned)blocks, kZ * 32, smem, s>>>(a);
-    return cudaGetLastError();
+    e = cudaGetLastError();
+    if (e == cudaSuccess && fuse) fs->done = true;
+    return e;
 }
 
 }  // namespace
@@ -381,12 +405,16 @@ extern "C" ecc_status ecc_compute_nd(ecc_plan_t p, const ecc_image_nd *img, int6
     a.status = p->status;
     a.smem_hist = p->nbins <= kSmemBinsMax;
     const bool top = p->d.complex_mode == ECC_TOPCELL_MIN;
-    cudaError_t e = es == 1 ? (top ? launch_walk4<unsigned char, true>(a, p->num_sms, s)
-                                   : launch_walk4<unsigned char, false>(a, p->num_sms, s))
-                            : (top ? launch_walk4<unsigned short, true>(a, p->num_sms, s)
-                                   : launch_walk4<unsigned short, false>(a, p->num_sms, s));
+    // the walker's last CTA scans small histograms itself; its finished-CTA
+    // count is a word of the plan's scheduling block the stencils leave free
+    a.done = p->sched + 3;
+    FusedScan fs{reinterpret_cast<long long *>(d_ecc), reinterpret_cast<long long *>(d_vcec), false};
+    cudaError_t e = es == 1 ? (top ? launch_walk4<unsigned char, true>(a, p->num_sms, s, &fs)
+                                   : launch_walk4<unsigned char, false>(a, p->num_sms, s, &fs))
+                            : (top ? launch_walk4<unsigned short, true>(a, p->num_sms, s, &fs)
+                                   : launch_walk4<unsigned short, false>(a, p->num_sms, s, &fs));
     p->last_launches = 1;
-    if (e == cudaSuccess) {
+    if (e == cudaSuccess && !fs.done) {
         e = launch_scan(p->acc, reinterpret_cast<long long *>(d_ecc), reinterpret_cast<long long *>(d_vcec), 1,
                         p->nbins, p->scan_ws(), p->status, s);
         ++p->last_launches;
