@@ -409,7 +409,7 @@ def run_gaussian_pipeline(args):
 
 def run_config1_latency(args):
     """C1, the 256x256 uint8 uniform image: too small to fill the GPU, so the
-    figure is the latency of one ecc_compute call (stencil + scan) measured
+    figure is the latency of one ecc_compute call (stencil and scan) measured
     with CUDA events on the stream, median of 200 calls, and the same for a
     call through ecc_compute_host (host image in, host ECC out)."""
     import numpy as np
