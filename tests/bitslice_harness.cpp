@@ -42,6 +42,24 @@ uint32_t h_kappa4d(const uint32_t *w81, int32_t *kappa)
     return nz;
 }
 
+// kappa4_nonzero for 32 voxels given as per-voxel counts (T0, Tp, Tm in
+// 0..12) and w-wins; returns the nonzero mask
+uint32_t h_kappa4_nonzero(const int32_t *t0, const int32_t *tp, const int32_t *tm, const int32_t *bp,
+                          const int32_t *bm)
+{
+    uint32_t T0[4] = {0, 0, 0, 0}, Tp[4] = {0, 0, 0, 0}, Tm[4] = {0, 0, 0, 0}, P = 0, M = 0;
+    for (int i = 0; i < 32; ++i) {
+        for (int k = 0; k < 4; ++k) {
+            T0[k] |= (uint32_t)((t0[i] >> k) & 1) << i;
+            Tp[k] |= (uint32_t)((tp[i] >> k) & 1) << i;
+            Tm[k] |= (uint32_t)((tm[i] >> k) & 1) << i;
+        }
+        P |= (uint32_t)(bp[i] & 1) << i;
+        M |= (uint32_t)(bm[i] & 1) << i;
+    }
+    return kappa4_nonzero(T0, Tp, Tm, P, M);
+}
+
 void h_count12(const uint32_t *x, uint32_t *o) { count12(x, o); }
 
 // w: 9 masks in [dy][dx] order; writes X[3] (kappa = X0 + X1 + 2 X2 - 3); returns nonzero mask

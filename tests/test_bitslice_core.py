@@ -224,3 +224,22 @@ def test_kappa4d_against_the_81_cells(h):
                 want = _kappa4_scalar(bits[:, x].reshape(3, 3, 3, 3).astype(int))
                 assert kap[x] == want
                 assert ((nz >> x) & 1) == (want != 0)
+
+
+def test_kappa4_nonzero_exhaustive(h):
+    """The 6-plane adder that decides kappa4 != 0 from the three chain counts
+    (each 0..12) and the two w-wins, against the integer formula, for every
+    combination."""
+    I32 = ctypes.POINTER(ctypes.c_int32)
+    h.h_kappa4_nonzero.argtypes = [I32] * 5
+    h.h_kappa4_nonzero.restype = ctypes.c_uint32
+    cases = np.array([(a, b, c, p, m) for a in range(13) for b in range(13) for c in range(13)
+                      for p in (0, 1) for m in (0, 1)], np.int32)
+    pad = (-len(cases)) % 32
+    cases = np.concatenate([cases, np.tile(cases[:1], (pad, 1))])
+    want = ((cases[:, 0] - 5) - cases[:, 3] * (cases[:, 1] - 5) - cases[:, 4] * (cases[:, 2] - 5)) != 0
+    for g in range(0, len(cases), 32):
+        blk = np.ascontiguousarray(cases[g:g + 32].T)
+        nz = h.h_kappa4_nonzero(*[blk[j].ctypes.data_as(I32) for j in range(5)])
+        got = np.array([(nz >> i) & 1 for i in range(32)], bool)
+        assert np.array_equal(got, want[g:g + 32]), g
