@@ -192,8 +192,10 @@ cudaError_t levels_enqueue(ecc_plan_s *p, const Geom &g, const float *d_levels, 
     dg.pitch_z = dp_z;
     HistDst h{p->acc, 0, p->nbins};
     if (p->d.flags & ECC_FLAG_COUNT_EMITTED) h.emitted = p->emitted;
-    if (e == cudaSuccess) e = launch_stencil(p, dg, 0, g.ndim == 3 ? g.nz : g.ny, h, s);
-    if (e == cudaSuccess) {
+    // the stencil's last CTA scans small histograms itself (fs.done)
+    FusedScan fs{p->stage_ecc, nullptr, false};
+    if (e == cudaSuccess) e = launch_stencil(p, dg, 0, g.ndim == 3 ? g.nz : g.ny, h, s, &fs);
+    if (e == cudaSuccess && !fs.done) {
         e = launch_scan(p->acc, p->stage_ecc, nullptr, 1, p->nbins, p->scan_ws(), p->status, s);
         ++p->last_launches;
     }
