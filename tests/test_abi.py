@@ -61,3 +61,24 @@ def test_python_image_descriptor_from_numpy():
     d = ecc._binding.host_image_desc(a)
     assert (d.ndim, d.dtype, list(d.dims)) == (3, ecc.ECC_U16, [5, 4, 5])
     assert d.row_pitch == 7 * 2 and d.slice_pitch == 6 * 7 * 2
+
+
+def test_null_plan_is_rejected_by_every_plan_entry_point(lib):
+    """Each entry point that takes a plan reports ECC_E_INVALID for a NULL
+    plan, with a message naming it, before it touches the device (so this
+    runs without a GPU)."""
+    inval = ecc.ECC_E_INVALID
+    calls = {
+        "ecc_compute_host": lambda: lib.ecc_compute_host(None, None, None, None),
+        "ecc_compute_stream": lambda: lib.ecc_compute_stream(None, None, None, 0, None),
+        "ecc_compute_levels": lambda: lib.ecc_compute_levels(None, None, None, 1, None, None),
+        "ecc_compute_nd": lambda: lib.ecc_compute_nd(None, None, None, None, None),
+        "ecc_pipeline_gaussian": lambda: lib.ecc_pipeline_gaussian(None, None, None, 13, 1, None, 1, None, None),
+        "ecc_status_get": lambda: lib.ecc_status_get(None, None),
+    }
+    for name, call in calls.items():
+        assert call() == inval, name
+        assert name.encode() in lib.ecc_last_error(), name
+    ms, n = ctypes.c_double(), ctypes.c_int64()
+    assert lib.ecc_plan_kernel_time(None, ctypes.byref(ms), ctypes.byref(n)) == inval
+    assert lib.ecc_plan_last_launches(None) == -1
