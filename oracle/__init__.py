@@ -12,7 +12,11 @@ several host threads and sums their histograms.
 
 Parity status: every function here is pinned by the ``-m "not gpu"`` tests in
 ``tests/test_oracle_pins.py`` (brute force on tiny inputs, Betti numbers by
-flood fill, closed forms, symmetries, and a mutation check).
+flood fill, closed forms, symmetries, and a mutation check), the float
+thresholds by ``tests/test_oracle_levels_pins.py``, the smoothing filter by
+``tests/test_oracle_blur_pins.py`` and the iterated pipeline by
+``tests/test_oracle_pipeline_pins.py`` (closed-form filters fix the order
+ECC-then-smooth and the round count).
 """
 from __future__ import annotations
 
