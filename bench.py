@@ -560,22 +560,7 @@ def run_serving(args):
     import paper_2203_09087_gb300 as ecc
     import synth
     reqs = synth.poisson_requests(2000.0, args.serve_seconds)
-    base2d = synth.smoothed_field((4096, 4096), 3.0, np.uint8, seed=41, device="cuda")
-    base8 = synth.smoothed_field((768, 768, 768), 3.0, np.uint8, seed=42, device="cuda")
-    base16 = synth.smoothed_field((768, 768, 768), 3.0, np.uint16, seed=43, device="cuda")
-    rng = np.random.default_rng(4)
-    views = []
-    for r in reqs:
-        s = r["shape"][0]
-        if len(r["shape"]) == 2:
-            o = [int(rng.integers(0, 4096 - s + 1)) for _ in range(2)]
-            o[1] -= o[1] % 16
-            views.append((base2d[o[0]:o[0] + s, o[1]:o[1] + s], 255))
-        else:
-            base, hi = (base8, 255) if r["dtype"] == "u8" else (base16, 65535)
-            o = [int(rng.integers(0, 768 - s + 1)) for _ in range(3)]
-            o[2] -= o[2] % 16
-            views.append((base[o[0]:o[0] + s, o[1]:o[1] + s, o[2]:o[2] + s], hi))
+    views = synth.serving_crops(reqs, synth.serving_bases(device="cuda"))
     vox = sum(int(v.numel()) for v, _ in views)
 
     def serve(replay_rate: bool):
@@ -610,6 +595,9 @@ def run_serving(args):
     mism_rt = [i for i, (a, b) in enumerate(zip(outs_seq, outs_rt)) if not np.array_equal(a, b)]
     mism_sat = [i for i, (a, b) in enumerate(zip(outs_seq, outs_sat)) if not np.array_equal(a, b)]
     same = not mism_rt and not mism_sat
+    if not same:
+        raise AssertionError(f"served results differ from the sequential plain path: nominal {mism_rt[:4]}, "
+                             f"saturating {mism_sat[:4]}")
     return {"workload": f"Poisson 2000 req/s x {args.serve_seconds:g} s (seed 4), 70% 2D u8 128^2-4096^2, "
                         "30% 3D u8/u16 64^3-768^3, crops of resident seeded fields",
             "requests": len(views), "voxels": vox,

@@ -37,8 +37,13 @@
  *    dims[0], Sec. 3.4).  Pitches are in bytes; 0 means dense.
  *  - Results are exact int64; there is no floating point anywhere.
  *  - Values outside [lo, hi] are reported on the device (ECC_E_RANGE from
- *    ecc_status_get) unless ECC_FLAG_NO_RANGE_CHECK is set; the offending
- *    voxels contribute nothing.
+ *    ecc_status_get): when [lo, hi] leaves out values of the element type,
+ *    every voxel is compared with both bounds.  A plan whose range is the
+ *    type's whole range (0..255 for ECC_U8, 0..65535 for ECC_U16) cannot
+ *    meet such a value and checks nothing.  ECC_FLAG_NO_RANGE_CHECK skips
+ *    the comparison of every voxel; an offending voxel whose signed cell
+ *    count is nonzero is then still reported.  Offending voxels never reach
+ *    the histogram.
  *  - A plan is used by one host thread at a time and by one stream at a
  *    time (calls on a plan are ordered on the stream they are issued to).
  *    The server (ecc_server_*) is thread-safe.
@@ -100,7 +105,7 @@ typedef struct ecc_image_nd {
 } ecc_image_nd;
 
 /* Plan flags. */
-#define ECC_FLAG_NO_RANGE_CHECK   0x1u  /* caller guarantees lo <= value <= hi */
+#define ECC_FLAG_NO_RANGE_CHECK   0x1u  /* caller guarantees lo <= value <= hi: skip the per-voxel check */
 #define ECC_FLAG_NO_AUTOTUNE      0x2u  /* use built-in tile defaults, never time candidates */
 #define ECC_FLAG_KERNEL_DIRECT    0x10u /* force the one-thread-per-voxel stencil kernel */
 #define ECC_FLAG_KERNEL_BITSLICE  0x20u /* force the bit-sliced stencil kernel (where it applies) */

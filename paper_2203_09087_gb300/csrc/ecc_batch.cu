@@ -82,7 +82,9 @@ struct BatchArgs {
     unsigned long long *acc;
     int32_t lo, nbins;
     int32_t chunk2d, chunk3d;
-    int32_t smem_hist, range_check;
+    int32_t smem_hist, range_check;  // range_check: the bins are guarded (range narrower than the type)
+    int32_t check_all;               // every output voxel is compared with [lo, hi]
+    uint32_t lo_bits, hi_bits;
     unsigned int *status;
 };
 
@@ -182,6 +184,8 @@ __device__ void run_tile(const BatchArgs &a, const BatchImage &im, long long loc
             uint32_t B[K];
             walk::planes_from_words<K>(wn, sh, B);
             if (y1 + 1 <= ye) sh = fetch(y1 + 1, wn);
+            if (a.check_all && y1 < ye && (~walk::in_range<K>(B, a.lo_bits, a.hi_bits) & out_x))
+                atomicOr(a.status, DEV_RANGE);
             wk.step(B, y1 < im.ny, y1 - 1 >= 0, y1 - 1 >= yb, out_x,
                     [&](uint32_t m, const uint32_t *X, const uint32_t *) {
                         // values of row y1-1, just read (cached)
@@ -238,16 +242,19 @@ __device__ void run_tile(const BatchArgs &a, const BatchImage &im, long long loc
         r0.P[K] = zb - 1 >= 0 ? e_row : 0xffffffffu;
         walk::complete_rows<K>(r0);
         sh = fetch(zb, wn);
+        uint32_t bad = 0;  // output voxels outside [lo, hi] (when checked)
         for (int64_t z1 = zb;; ++z1) {
             walk::planes_from_words<K>(wn, sh, r1.P);
             r1.P[K] = z1 < im.nz ? e_row : 0xffffffffu;
             if (z1 + 1 <= ze) sh = fetch(z1 + 1, wn);
+            if (a.check_all && z1 < ze) bad |= ~walk::in_range<K>(r1.P, a.lo_bits, a.hi_bits) & out_x;
             walk::complete_rows<K>(r1);
             vals = im.data + (z1 - 1) * im.pitch_z + (row_ok ? y : 0) * im.pitch_y + xw * (K / 8);
             wk.step(r0, r1, z1 - 1 >= zb, out_x, emit);
             r0 = r1;
             if (z1 >= ze) break;
         }
+        if (a.check_all && __any_sync(0xffffffffu, bad != 0u) && lane == 0) atomicOr(a.status, DEV_RANGE);
     }
 }
 
@@ -314,6 +321,17 @@ __global__ void __launch_bounds__(kBatchWarps * 32, 4) batch_kernel(BatchArgs a)
     flush();
 }
 
+// The bins are guarded whenever the plan's range leaves out values of its
+// type; every output voxel is compared with the bounds unless the plan opted
+// out (ECC_FLAG_NO_RANGE_CHECK).
+void set_range(BatchArgs &args, const ecc_plan_s *p)
+{
+    args.range_check = walk::range_is_narrow(args.lo, args.nbins, p->d.dtype == ECC_U16 ? 2 : 1);
+    args.check_all = args.range_check && !(p->d.flags & ECC_FLAG_NO_RANGE_CHECK);
+    args.lo_bits = (uint32_t)args.lo;
+    args.hi_bits = (uint32_t)(args.lo + args.nbins - 1);
+}
+
 template <int K, bool TOP>
 cudaError_t batch_instance(void **fn, size_t smem, int *per_sm)
 {
@@ -354,7 +372,7 @@ cudaError_t capture_graph(ecc_plan_s *p, BatchState *b)
     args.chunk2d = b->chunk2d;
     args.chunk3d = b->chunk3d;
     args.smem_hist = smem_hist;
-    args.range_check = !(p->d.flags & ECC_FLAG_NO_RANGE_CHECK);
+    set_range(args, p);
     args.status = p->status;
 
     e = cudaGraphCreate(&b->graph, 0);
@@ -467,7 +485,7 @@ cudaError_t launch_batch_single(ecc_plan_s *p, const Geom &g, const HistDst &h, 
     args.chunk2d = b->chunk2d;
     args.chunk3d = b->chunk3d;
     args.smem_hist = b->smem_hist;
-    args.range_check = !(p->d.flags & ECC_FLAG_NO_RANGE_CHECK);
+    set_range(args, p);
     args.status = p->status;
     const BatchImage im{g.data, g.nx, g.ny, g.nz, g.pitch_y, g.pitch_z, g.ndim, g.esize};
     init_single<<<1, 1, 0, s>>>(args, im);

@@ -26,7 +26,8 @@ struct DirectArgs {
     HistDst h;
     unsigned int *status;
     int smem_hist;
-    int range_check;
+    int range_check;  // the bins are guarded (range narrower than the type)
+    int check_all;    // every voxel is compared with [lo, hi]
 };
 
 template <typename T>
@@ -56,12 +57,14 @@ __device__ __forceinline__ bool beats(int c, int q, bool later, bool exists)
 // active threads of a warp are converged here).
 __device__ __forceinline__ void add_bin(const DirectArgs &a, int *s_hist, int value, int kappa)
 {
-    int bin = kappa ? value - a.h.lo : -1;
-    if (kappa && a.range_check && (unsigned)bin >= (unsigned)a.h.nbins) {
-        atomicOr(a.status, DEV_RANGE);
-        bin = -1;
-    }
     const unsigned active = __activemask();
+    int bin = value - a.h.lo;
+    const bool bad = a.range_check && (unsigned)bin >= (unsigned)a.h.nbins;
+    // a voxel outside [lo, hi] is reported when every voxel is checked, or
+    // when it would have contributed; it never reaches the bins
+    const unsigned report = __ballot_sync(active, bad && (a.check_all || kappa));
+    if (report && (int)(threadIdx.x & 31) == __ffs(active) - 1) atomicOr(a.status, DEV_RANGE);
+    if (bad || !kappa) bin = -1;
     if (a.h.emitted) {
         const unsigned nz = __ballot_sync(active, kappa != 0);
         if (nz && (int)(threadIdx.x & 31) == __ffs(active) - 1) atomicAdd(a.h.emitted, (unsigned long long)__popc(nz));
@@ -266,7 +269,8 @@ cudaError_t launch_direct(const Geom &g, int64_t outer_begin, int64_t outer_end,
     a.h = h;
     a.status = status;
     a.smem_hist = h.nbins <= 4096;
-    a.range_check = range_check;
+    a.range_check = (g.esize == 1 ? 255 : 65535) > (int64_t)h.lo + h.nbins - 1 || h.lo > 0;
+    a.check_all = range_check && a.range_check;
     const bool top = complex_mode == ECC_TOPCELL_MIN;
     if (g.esize == 1)
         return top ? launch_typed<unsigned char, true>(a, num_sms, s)

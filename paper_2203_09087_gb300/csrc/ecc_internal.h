@@ -103,6 +103,11 @@ cudaError_t launch_bitslice(const Geom &g, int64_t outer_begin, int64_t outer_en
                             int complex_mode, bool range_check, unsigned int *status, unsigned int *sched,
                             int num_sms, int tune_param, cudaStream_t s, FusedScan *fs = nullptr);
 
+// The 3D bit-sliced kernel (ecc_bs3d.cu); tune = warps per CTA (4 or 8).
+cudaError_t launch_bs3d(const Geom &g, int64_t zb, int64_t ze, const HistDst &h, int mode, bool range_check,
+                        unsigned int *status, unsigned int *sched, int num_sms, int tune, cudaStream_t s,
+                        FusedScan *fs);
+
 // Segmented inclusive scan of n_seg * nbins int64 values (segment i =
 // elements [i*nbins, (i+1)*nbins)).  Reads acc, writes ecc (and vcec if not
 // null), and zeroes acc for the next call.

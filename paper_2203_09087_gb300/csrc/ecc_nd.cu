@@ -67,7 +67,9 @@ struct Walk4Args {
     int32_t remy;        // rows left below the full tiles (0..29)
     int32_t pack;        // partial tiles (remy rows + 2 halo lanes) per warp
     HistDst h;
-    int32_t smem_hist, range_check;
+    int32_t smem_hist, range_check;  // range_check: the bins are guarded (range narrower than the type)
+    int32_t check_all;               // every output voxel is compared with [lo, hi]
+    uint32_t lo_bits, hi_bits;
     unsigned int *status;
     long long *ecc_out;    // non-null: the last CTA also scans the bins (at most kFusedScanMaxBins)
     long long *vcec_out;
@@ -100,6 +102,7 @@ __global__ void __launch_bounds__(z_group<T>() * 32) walk4d_kernel(const Walk4Ar
     const int64_t nw = a.n[0], nz = a.n[1], ny = a.n[2], nx = a.n[3];
     const int64_t row_bytes = nx * (int64_t)sizeof(T);
     unsigned n_emitted = 0;
+    uint32_t bad = 0;  // output voxels outside [lo, hi] (when checked)
 
     // slot j of hyperplane buffer h holds slice z0 - 1 + j; plane k at [k * 32]
     auto slot = [&](int h, int j) { return SL + (h * (kZ + 2) + j) * KP * 32 + lane; };
@@ -189,6 +192,7 @@ __global__ void __launch_bounds__(z_group<T>() * 32) walk4d_kernel(const Walk4Ar
             const int par = (int)((w - w0 + 1) & 1), prv = par ^ 1;
             uint32_t B0[KP];
             load_hyperplane(w + 1, hB, B0);
+            if (a.check_all && w + 1 < w1 && z < nz) bad |= ~walk::in_range<K>(B0, a.lo_bits, a.hi_bits) & out;
             __syncthreads();
             const bool emit_step = w >= w0;   // the first step only fills the carried state
             uint32_t W[3][3][3], T0[4], Tm[4], Tp[4], bm = 0, bp = 0;
@@ -280,6 +284,7 @@ __global__ void __launch_bounds__(z_group<T>() * 32) walk4d_kernel(const Walk4Ar
         const unsigned n = __reduce_add_sync(0xffffffffu, n_emitted);
         if (lane == 0 && n) atomicAdd(a.h.emitted, (unsigned long long)n);
     }
+    if (a.check_all && __any_sync(0xffffffffu, bad != 0u) && lane == 0) atomicOr(a.status, DEV_RANGE);
     __syncthreads();
     if (a.smem_hist)
         for (int i = threadIdx.x; i < a.h.nbins; i += blockDim.x)
@@ -401,7 +406,12 @@ extern "C" ecc_status ecc_compute_nd(ecc_plan_t p, const ecc_image_nd *img, int6
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     a.h = HistDst{p->acc, p->d.lo, p->nbins};
     if (p->d.flags & ECC_FLAG_COUNT_EMITTED) a.h.emitted = p->emitted;
-    a.range_check = !(p->d.flags & ECC_FLAG_NO_RANGE_CHECK);
+    // the bins are guarded whenever values can fall outside them; every
+    // output voxel is compared with the bounds unless the plan opted out
+    a.range_check = walk::range_is_narrow(p->d.lo, p->nbins, es);
+    a.check_all = a.range_check && !(p->d.flags & ECC_FLAG_NO_RANGE_CHECK);
+    a.lo_bits = (uint32_t)p->d.lo;
+    a.hi_bits = (uint32_t)(p->d.hi);
     a.status = p->status;
     a.smem_hist = p->nbins <= kSmemBinsMax;
     const bool top = p->d.complex_mode == ECC_TOPCELL_MIN;

@@ -3,10 +3,10 @@
 //
 // Keys: GPU name, SM count, element type and complex.  For each key it
 // chooses
-//   * the 3D bit-sliced kernel's windows per CTA and number of shared
-//     histogram copies (candidates 6x2, 6x1, 4x2, 3x1), timed in three
-//     interleaved rounds on a synthetic 512x512x256 volume, 3x1 kept unless
-//     another is at least 3 % faster;
+//   * the 3D bit-sliced kernel's warps per CTA (4 or 8: warps sharing one
+//     shared histogram and one flush), timed in three interleaved rounds on
+//     a synthetic 512x512x256 volume, 4 kept unless 8 is at least 3 %
+//     faster;
 //   * the batched kernel's rows per 2D tile (16, 32, 64) and planes per 3D
 //     tile (8, 16, 32), timed on a synthetic uneven batch.
 // Results are kept for the process and appended to a text cache
@@ -30,7 +30,7 @@
 namespace ecc {
 namespace {
 
-// "<key>|3d" -> {tp3d, 0}; "<key>|batch" -> {chunk2d, chunk3d}
+// "<key>|3dw" -> {warps per CTA, 0}; "<key>|batch" -> {chunk2d, chunk3d}
 struct Choice {
     int a = 0, b = 0;
 };
@@ -112,7 +112,7 @@ using namespace ecc;
 
 void ecc_plan_s::autotune()
 {
-    // explicit overrides (benchmark sweeps): ECC_TILE3D = 61 | 62 | 42 | 31
+    // explicit override (benchmark sweeps): ECC_TILE3D = 4 | 8 warps per CTA
     if (const char *t = std::getenv("ECC_TILE3D")) {
         const int v = std::atoi(t);
         tuned[1] = tuned[3] = v;
@@ -132,7 +132,7 @@ void ecc_plan_s::autotune()
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
         load_cache();
-        auto it = g_tuned.find(key + "|3d");
+        auto it = g_tuned.find(key + "|3dw");
         if (std::getenv("ECC_TILE3D")) {
             need3d = false;
         } else if (it != g_tuned.end()) {
@@ -152,11 +152,9 @@ void ecc_plan_s::autotune()
     if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return;
     const bool range = !(d.flags & ECC_FLAG_NO_RANGE_CHECK);
     if (need3d) {
-        // 3D single-image kernel on a synthetic 512x512x256 volume.  Which
-        // tile wins depends on how its CTAs fill waves, so the volume has the
-        // proportions of large real volumes: on 512x256x192 the 4x2 and 3x1
-        // tiles timed alike and boxes differed in their pick, while at
-        // 512^3 3x1 is 8 % faster.
+        // 3D single-image kernel on a synthetic 512x512x256 volume, with the
+        // proportions of large real volumes (how the warps fill the GPU
+        // depends on the shape).
         const int nx = 512, ny = 512, nz = 256;
         const int64_t n = (int64_t)nx * ny * nz;
         unsigned char *buf = nullptr;
@@ -166,29 +164,19 @@ void ecc_plan_s::autotune()
             Geom g{buf, nz, ny, nx, (int64_t)nx * es, (int64_t)nx * ny * es, 3, es};
             HistDst h{acc, d.lo, nbins};
             // three interleaved rounds, each candidate's best: a single pass
-            // in a fixed order was at the mercy of clock ramp-up and noise
-            // (boxes differed in their pick, and the slower picks cost ~10 %
-            // at 512^3)
-            const int cands[4] = {62, 61, 42, 31};
-            float best_of[4] = {1e30f, 1e30f, 1e30f, 1e30f};
+            // in a fixed order is at the mercy of clock ramp-up and noise
+            const int cands[2] = {4, 8};
+            float best_of[2] = {1e30f, 1e30f};
             for (int round = 0; round < 3; ++round)
-                for (int ci = 0; ci < 4; ++ci) {
+                for (int ci = 0; ci < 2; ++ci) {
                     const int tp = cands[ci];
                     const float ms = time_ms(
                         [&] { launch_bitslice(g, 0, nz, h, d.complex_mode, range, status, sched, num_sms, tp, s); },
                         s, 5);
                     best_of[ci] = ms < best_of[ci] ? ms : best_of[ci];
                 }
-            // 3x1 unless another tile is clearly faster: 3x1 and 4x2 can time
-            // within noise here while 3x1 is 8 % faster at 512^3 uint8 and
-            // 3.5 % at 1024^3 uint16 (measured), so a near-tie keeps 3x1
-            c.a = 31;
-            float best = best_of[3] * 0.97f;
-            for (int ci = 0; ci < 3; ++ci)
-                if (best_of[ci] < best) {
-                    best = best_of[ci];
-                    c.a = cands[ci];
-                }
+            // 4 warps per CTA unless 8 is at least 3 % faster
+            c.a = best_of[1] < 0.97f * best_of[0] ? 8 : 4;
             cudaStreamSynchronize(s);
             cudaFree(buf);
         }
@@ -198,8 +186,8 @@ void ecc_plan_s::autotune()
         cudaGetLastError();
         tuned[key3d] = c.a;
         std::lock_guard<std::mutex> lk(g_tune_mu);
-        g_tuned[key + "|3d"] = c;
-        save_choice(key + "|3d", c);
+        g_tuned[key + "|3dw"] = c;
+        save_choice(key + "|3dw", c);
     }
     if (needb) {
         // batched kernel on an uneven synthetic batch (2D and 3D images in one buffer)

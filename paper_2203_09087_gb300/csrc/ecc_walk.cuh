@@ -123,6 +123,33 @@ __device__ __forceinline__ void planes_from_words(const uint32_t *w, int sh, uin
         bs::transpose_u16(raw, planes);
 }
 
+// ------------------------------------------------------------------ gray range
+
+// Mask of voxels with lo <= v <= hi over K value planes, the bounds given as
+// their bits (bit k of lo_bits / hi_bits is bit k of the bound): two
+// bit-serial comparisons with broadcast planes.
+template <int K>
+__device__ __forceinline__ uint32_t in_range(const uint32_t *v, uint32_t lo_bits, uint32_t hi_bits)
+{
+    uint32_t cl = v[0] | ((lo_bits & 1u) ? 0u : ~0u);  // v >= lo
+    uint32_t ch = ((hi_bits & 1u) ? ~0u : 0u) | ~v[0];  // hi >= v
+#pragma unroll
+    for (int k = 1; k < K; ++k) {
+        const uint32_t l = ((lo_bits >> k) & 1u) ? ~0u : 0u, h = ((hi_bits >> k) & 1u) ? ~0u : 0u;
+        cl = (v[k] & ~l) | ((v[k] | ~l) & cl);
+        ch = (h & ~v[k]) | ((h | ~v[k]) & ch);
+    }
+    return cl & ch;
+}
+
+// Does [lo, lo + nbins) leave out values of a K-bit type?  Only then can an
+// image value fall outside the range, and only then are voxels checked.
+__host__ __device__ inline bool range_is_narrow(int lo, int nbins, int esize)
+{
+    const long long type_max = esize == 1 ? 255 : 65535;
+    return lo > 0 || (long long)lo + nbins - 1 < type_max;
+}
+
 // ------------------------------------------------------------------ histogram
 
 // One warp's histogram destination: shared int32 bins (flushed per CTA) or,

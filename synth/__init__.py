@@ -183,3 +183,31 @@ def poisson_requests(rate_hz: float, duration_s: float, seed: int = 4, frac_2d: 
             shape, dt = (s, s, s), ("u8" if rng.uniform() < 0.5 else "u16")
         out.append({"t": t, "shape": shape, "dtype": dt, "sigma": float(rng.uniform(1.0, 6.0))})
     return out
+
+
+def serving_bases(device="cuda"):
+    """Resident seeded fields the serving requests are cut from: one 4096^2
+    uint8 image and one 768^3 volume each of uint8 and uint16 (sigma 3)."""
+    return {"2d": smoothed_field((4096, 4096), 3.0, np.uint8, seed=41, device=device),
+            "u8": smoothed_field((768, 768, 768), 3.0, np.uint8, seed=42, device=device),
+            "u16": smoothed_field((768, 768, 768), 3.0, np.uint16, seed=43, device=device)}
+
+
+def serving_crops(reqs, bases, seed: int = 4):
+    """One (view, hi) per request: a crop of the request's shape from its base
+    field at a seeded origin, the innermost origin rounded down to a multiple
+    of 16 elements.  Views share the bases' storage."""
+    rng = np.random.default_rng(seed)
+    views = []
+    for r in reqs:
+        s = r["shape"][0]
+        if len(r["shape"]) == 2:
+            o = [int(rng.integers(0, 4096 - s + 1)) for _ in range(2)]
+            o[1] -= o[1] % 16
+            views.append((bases["2d"][o[0]:o[0] + s, o[1]:o[1] + s], 255))
+        else:
+            base, hi = (bases["u8"], 255) if r["dtype"] == "u8" else (bases["u16"], 65535)
+            o = [int(rng.integers(0, 768 - s + 1)) for _ in range(3)]
+            o[2] -= o[2] % 16
+            views.append((base[o[0]:o[0] + s, o[1]:o[1] + s, o[2]:o[2] + s], hi))
+    return views

@@ -2,6 +2,7 @@
 // tests (tests/test_bitslice_core.py).  Built with g++; no CUDA needed.
 #include <stdint.h>
 
+#include "ecc_bitlogic.cuh"
 #include "ecc_bitslice.cuh"
 
 using namespace ecc::bs;
@@ -70,4 +71,32 @@ uint32_t h_kappa2d(const uint32_t *w9, uint32_t *X)
     return kappa2d(w, X);
 }
 
+
+// ---- the 3D walker's bit logic (ecc_bitlogic.cuh) with multiply shifts and
+// explicit three-input operations
+
+void h_w3_transpose_u8(const uint32_t *r, uint32_t *p) { ecc::walk3::transpose_u8(r, p, ecc::walk3::make_mul()); }
+void h_w3_transpose_u16(const uint32_t *r, uint32_t *p) { ecc::walk3::transpose_u16(r, p, ecc::walk3::make_mul()); }
+uint32_t h_w3_ge8(const uint32_t *a, const uint32_t *b) { return ecc::walk3::ge<8>(a, b); }
+uint32_t h_w3_ge16(const uint32_t *a, const uint32_t *b) { return ecc::walk3::ge<16>(a, b); }
+void h_w3_count12(const uint32_t *x, uint32_t *o) { ecc::walk3::count12(x, o); }
+
+// The walker's cell count from the 27 wins w[dz][dy][dx] (the centre unused),
+// handed over in the walker's polarities; returns the nonzero mask, writes T.
+uint32_t h_w3_kappa3(const uint32_t *w27, uint32_t out_x, uint32_t *T)
+{
+    uint32_t w[3][3][3];
+    for (int i = 0; i < 27; ++i) w[i / 9][(i / 3) % 3][i % 3] = w27[i];
+    uint32_t up[3][3], nW[3][3], sF[3], sD[3];
+    for (int dy = 0; dy < 3; ++dy)
+        for (int dx = 0; dx < 3; ++dx) {
+            up[dy][dx] = w[2][dy][dx];
+            nW[dy][dx] = ~w[0][dy][dx];
+        }
+    for (int dx = 0; dx < 3; ++dx) {
+        sF[dx] = w[1][2][dx];
+        sD[2 - dx] = ~w[1][0][dx];
+    }
+    return ecc::walk3::kappa3w(up, nW, ~w[1][1][0], w[1][1][2], sF, sD, out_x, T);
+}
 }

@@ -243,3 +243,78 @@ def test_kappa4_nonzero_exhaustive(h):
         nz = h.h_kappa4_nonzero(*[blk[j].ctypes.data_as(I32) for j in range(5)])
         got = np.array([(nz >> i) & 1 for i in range(32)], bool)
         assert np.array_equal(got, want[g:g + 32]), g
+
+
+# ---------------------------------------------------------------------------
+# The 3D walker's bit logic (ecc_bitlogic.cuh): explicit three-input logic
+# operations and multiply shifts, against naive code and the plain forms.
+
+def _w3(h):
+    u32p = ctypes.POINTER(ctypes.c_uint32)
+    for n in ("h_w3_transpose_u8", "h_w3_transpose_u16", "h_w3_count12"):
+        getattr(h, n).argtypes = [u32p, u32p]
+    for n in ("h_w3_ge8", "h_w3_ge16"):
+        getattr(h, n).argtypes = [u32p, u32p]
+        getattr(h, n).restype = ctypes.c_uint32
+    h.h_w3_kappa3.argtypes = [u32p, ctypes.c_uint32, u32p]
+    h.h_w3_kappa3.restype = ctypes.c_uint32
+    return h
+
+
+@pytest.mark.parametrize("bits", [8, 16])
+def test_walker_transpose_matches_naive(h, bits):
+    w3 = _w3(h)
+    rng = np.random.default_rng(40 + bits)
+    dt = np.uint8 if bits == 8 else np.uint16
+    fn = w3.h_w3_transpose_u8 if bits == 8 else w3.h_w3_transpose_u16
+    for _ in range(200):
+        vox = rng.integers(0, 1 << bits, size=32, dtype=dt)
+        r = np.frombuffer(vox.tobytes(), dtype=np.uint32).copy()
+        p = np.zeros(bits, np.uint32)
+        fn(_p(r), _p(p))
+        assert np.array_equal(p, planes_naive(vox, bits))
+
+
+@pytest.mark.parametrize("bits", [8, 16])
+def test_walker_ge_matches_naive(h, bits):
+    w3 = _w3(h)
+    rng = np.random.default_rng(50 + bits)
+    fn = w3.h_w3_ge8 if bits == 8 else w3.h_w3_ge16
+    for levels in (2, 5, 1 << bits):
+        for _ in range(100):
+            a = rng.integers(0, levels, size=32)
+            b = rng.integers(0, levels, size=32)
+            pa, pb = planes_naive(a, bits), planes_naive(b, bits)
+            want = sum(1 << x for x in range(32) if a[x] >= b[x])
+            assert fn(_p(pa), _p(pb)) == want
+
+
+def test_walker_count12_matches_plain(h):
+    w3 = _w3(h)
+    rng = np.random.default_rng(60)
+    for _ in range(300):
+        x = rng.integers(0, 1 << 32, size=12, dtype=np.uint64).astype(np.uint32)
+        o1 = np.zeros(4, np.uint32)
+        o2 = np.zeros(4, np.uint32)
+        h.h_count12(_p(x), _p(o1))
+        w3.h_w3_count12(_p(x), _p(o2))
+        assert np.array_equal(o1, o2)
+
+
+def test_walker_cell_count_equals_plain_on_random_and_structured_wins(h):
+    """kappa3w (the walker's polarities, explicit truth tables) against
+    bs::kappa3d, which the chain identity pins on all 2^26 win patterns."""
+    w3 = _w3(h)
+    rng = np.random.default_rng(61)
+    for density in (0.05, 0.3, 0.5, 0.7, 0.95):
+        for _ in range(200):
+            w = (rng.uniform(size=(27, 32)) < density)
+            w27 = np.array([sum(int(w[i, x]) << x for x in range(32)) for i in range(27)], np.uint32)
+            w27[13] = 0
+            t1 = np.zeros(4, np.uint32)
+            t2 = np.zeros(4, np.uint32)
+            nz1 = h.h_kappa3d(_p(w27), _p(t1))
+            out_x = int(rng.integers(0, 1 << 32))
+            nz2 = w3.h_w3_kappa3(_p(w27), out_x, _p(t2))
+            assert np.array_equal(t1, t2)
+            assert nz2 == (nz1 & out_x)

@@ -70,9 +70,27 @@ def test_batch_repeated_and_resized():
             assert np.array_equal(got[k], oracle.ecc(img, 0, 255))
 
 
-def test_batch_full_size_config4_sampled():
-    """The uneven 4096 + 256 batch at full size: every row equals the
-    one-launch-per-image path; a seeded sample of rows equals the oracle."""
+def _oracle_many(arrays, his, mode=oracle.VERTEX):
+    """The single-threaded oracle on every host array, several arrays at a
+    time on the host's cores (the C library releases the GIL); arrays above
+    32 M voxels run slab-parallel on all cores instead."""
+    import os
+    from concurrent.futures import ThreadPoolExecutor
+    cores = os.cpu_count() or 4
+    out = [None] * len(arrays)
+    small = [k for k, a in enumerate(arrays) if a.size <= 32 << 20]
+    with ThreadPoolExecutor(max_workers=cores) as ex:
+        for k, r in zip(small, ex.map(lambda k: oracle.ecc(arrays[k], 0, his[k], mode), small)):
+            out[k] = r
+    for k, a in enumerate(arrays):
+        if out[k] is None:
+            out[k] = oracle.ecc_from_vcec(oracle.vcec_parallel(a, 0, his[k], mode, threads=cores))
+    return out
+
+
+def test_batch_full_size_config4_every_row():
+    """The uneven 4096 + 256 batch at full size (C4): every row equals the
+    oracle, and the one-launch-per-image path gives the same rows."""
     import synth
     ecc = ecc_mod()
     specs = synth.batch_specs()
@@ -83,11 +101,39 @@ def test_batch_full_size_config4_sampled():
     got_b = ecc.ecc_compute_batch(plan_b, imgs).cpu().numpy()
     got_p = ecc.ecc_compute_batch(plan_p, imgs).cpu().numpy()
     ecc.ecc_status_get(plan_b)
+    ecc.ecc_status_get(plan_p)
     assert np.array_equal(got_b, got_p)
-    rng = np.random.default_rng(99)
-    for k in rng.choice(len(imgs), size=40, replace=False).tolist() + [len(imgs) - 1]:
-        host = imgs[k].cpu().numpy()
-        assert np.array_equal(got_b[k], oracle.ecc(host, 0, 255)), k
+    want = _oracle_many([t.cpu().numpy() for t in imgs], [255] * len(imgs))
+    bad = [k for k in range(len(imgs)) if not np.array_equal(got_b[k], want[k])]
+    assert not bad, (len(bad), bad[:5])
+
+
+def test_serving_config5_sample_against_oracle():
+    """A seeded sample of 100 requests drawn from the serving workload (C5:
+    the 60 s Poisson list, 2D uint8 128^2-4096^2 and 3D uint8/uint16
+    64^3-768^3, crops of the resident seeded fields) served together under
+    the 120 GB budget: every result equals the oracle."""
+    import synth
+    ecc = ecc_mod()
+    reqs = synth.poisson_requests(2000.0, 60.0)
+    views = synth.serving_crops(reqs, synth.serving_bases(device="cuda"))
+    rng = np.random.default_rng(5)
+    pick = sorted(rng.choice(len(views), size=100, replace=False).tolist())
+    # the largest shapes of the distribution are in the sample too
+    big2 = max((k for k in range(len(reqs)) if len(reqs[k]["shape"]) == 2), key=lambda k: reqs[k]["shape"][0])
+    big3 = max((k for k in range(len(reqs)) if len(reqs[k]["shape"]) == 3), key=lambda k: reqs[k]["shape"][0])
+    pick = sorted(set(pick) | {big2, big3})
+    sample = [views[k] for k in pick]
+    assert {str(v.dtype) for v, _ in sample} == {"torch.uint8", "torch.uint16"}
+    srv = ecc.ecc_server_create(120 << 30, n_streams=4, max_batch=64)
+    outs = [np.zeros(hi + 1, np.int64) for _, hi in sample]
+    tickets = [ecc.ecc_submit(srv, v, 0, hi, out=outs[i]) for i, (v, hi) in enumerate(sample)]
+    for t in tickets:
+        assert ecc.ecc_wait(srv, t, 600_000_000) == ecc.ECC_OK
+    ecc.ecc_server_destroy(srv)
+    want = _oracle_many([v.contiguous().cpu().numpy() for v, _ in sample], [hi for _, hi in sample])
+    bad = [pick[i] for i in range(len(sample)) if not np.array_equal(outs[i], want[i])]
+    assert not bad, bad[:5]
 
 
 # ------------------------------------------------------------------ serving
