@@ -16,8 +16,13 @@ Also reported on the same JSON line:
                 back), copies inside the timed region;
   cpu_baseline  the CPU oracle (as it stands) on a bounded slab of the same
                 volume, on all host cores;
-  batched, serving  optional (--extras): the uneven-batch and serving
-                workloads, summarized.
+  config1, single_u16, batched, serving
+                the other configurations (C1 latency, C3 1024^3 uint16, C4
+                uneven batch against one launch per image, C5 Poisson serving
+                with p50/p99 and a saturating replay), each with its own
+                timing; --main-only leaves them out, --extras adds the
+                NEXT-row workloads (float thresholds, smoothing pipeline,
+                top-cell and 4D, one-core CPU baselines).
 
 ``--impl reference`` times the CPU oracle on the same workload (bounded slab
 samples per step) and prints the same line with "impl": "reference".
@@ -34,6 +39,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 from pathlib import Path
 
@@ -65,8 +71,8 @@ def _traffic_for(kernel_digest: str):
     return ent.get("dram_bytes_per_launch")
 
 
-STENCIL_SOURCES = ("ecc_bitslice.cu", "ecc_bitslice.cuh", "ecc_walk.cuh", "ecc_sync.cuh", "ecc_internal.h",
-                   "ecc_scan_block.cuh")
+STENCIL_SOURCES = ("ecc_bs3d.cu", "ecc_walk3.cuh", "ecc_bitlogic.cuh", "ecc_bitslice.cuh", "ecc_walk.cuh",
+                   "ecc_sync.cuh", "ecc_internal.h", "ecc_scan_block.cuh")
 
 
 def _kernel_digest():
@@ -615,7 +621,8 @@ def run_serving(args):
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--gpus", type=int, default=None,
+                    help="GPUs (one rank each); default: WORLD_SIZE under a launcher, else 1")
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
@@ -623,14 +630,29 @@ def main():
     ap.add_argument("--no-cpu", action="store_true", help="skip the cpu_baseline leg")
     ap.add_argument("--extras", action="store_true", help="also run the batched and serving workloads")
     ap.add_argument("--shape", default="512,512,512")
-    ap.add_argument("--serve-seconds", type=float, default=8.0,
-                    help="duration of the Poisson request stream in --extras (configuration: 60)")
+    ap.add_argument("--serve-seconds", type=float, default=60.0,
+                    help="duration of the serving workload's Poisson request stream (the configuration's 60 s)")
+    ap.add_argument("--main-only", action="store_true",
+                    help="only the headline 512^3 workload (no C1/C3/C4/C5 keys)")
     ap.add_argument("--quick", action="store_true",
                     help="profiler runs: no one-second warm-up floor, no e2e and CPU legs")
     ap.add_argument("--only-4d", type=int, default=0, metavar="SIDE",
                     help="profiler runs: only the 4D case SIDE^4 uint8 (three calls after the checked one)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
+    ws_env = int(os.environ.get("WORLD_SIZE", "1"))
+    if args.gpus is None:
+        args.gpus = ws_env
+    if "WORLD_SIZE" in os.environ and ws_env != args.gpus:
+        print(f"bench.py: --gpus {args.gpus} but WORLD_SIZE={ws_env}: launch one rank per GPU, "
+              f"--nproc-per-node equal to --gpus", file=sys.stderr)
+        return 2
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ:
+        # one process per GPU: relaunch under torch.distributed.run
+        cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", f"--nproc-per-node={args.gpus}",
+               "--master-addr", "127.0.0.1", "--master-port", os.environ.get("MASTER_PORT", "29531"),
+               str(ROOT / "bench.py"), *sys.argv[1:]]
+        return subprocess.call(cmd)
     if args.impl == "reference":
         return run_reference(args)
     if args.only_4d:
@@ -658,14 +680,15 @@ def main():
     l2 = torch.cuda.get_device_properties(local).L2_cache_size
     flush = torch.empty(2 * l2 + (1 << 20), dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
-    os.makedirs(ROOT / "gpurun_out", exist_ok=True)
 
     # correctness guard on the benchmarked volume: last ECC value of a full box is 1
     ecc.ecc_compute(plan, vol, out)
     ecc.ecc_status_get(plan)
     assert int(out[-1].item()) == 1
 
-    sampler = ClockSampler(str(ROOT / "gpurun_out" / f"clocks_rank{rank}.csv"))
+    clock_fd, clock_path = tempfile.mkstemp(prefix=f"ecc_clocks_rank{rank}_", suffix=".csv")
+    os.close(clock_fd)
+    sampler = ClockSampler(clock_path)
     with sampler:
         # warm-up (at least W steps and about a second, so clocks are sampled under load)
         t_end = time.perf_counter() + (0.0 if args.quick else 1.0)
@@ -760,6 +783,7 @@ def main():
                     "path": "ecc_compute_host, pinned host input, chunked H2D overlapped with kernels"},
             "gpu_launches": launches_per_step * args.steps,
             "clocks": sampler.summary()}
+    os.unlink(clock_path)
     # voxels with a nonzero signed count (the histogram insertions), from one
     # extra counting call outside the timed region
     cplan = ecc.ecc_plan("u8", 0, 255, max_voxels=nvox, flags=ecc.ECC_FLAG_COUNT_EMITTED)
@@ -774,16 +798,18 @@ def main():
         host_vol = vol.cpu().numpy()
         line["cpu_baseline"] = cpu_oracle_sample(host_vol)
         line["cpu_baseline_1core"] = cpu_oracle_sample(host_vol, budget_s=4.0, threads=1)
+    if rank == 0 and not args.main_only and not args.quick:
+        # the other configurations, each with its own timing
+        line["config1"] = run_config1_latency(args)       # C1: 256^2 uint8 latency
+        line["single_u16"] = run_single_u16(args)        # C3: 1024^3 uint16
+        line["batched"] = run_batched(args)              # C4: uneven batch vs one launch per image
+        line["serving"] = run_serving(args)              # C5: Poisson stream, p50/p99, saturating replay
     if args.extras and rank == 0:
-        line["batched"] = run_batched(args)
-        line["single_u16"] = run_single_u16(args)
         line["float_levels"] = run_float_levels(args)
         line["gaussian_pipeline"] = run_gaussian_pipeline(args)
         line["topcell_and_4d"] = run_topcell_and_4d(args)
-        line["config1"] = run_config1_latency(args)
         if not args.no_cpu:
             line["cpu_baselines_1core"] = run_cpu_baselines(args)
-        line["serving"] = run_serving(args)
     if rank == 0:
         print(json.dumps(line))
     if dist:

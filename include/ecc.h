@@ -264,8 +264,14 @@ ecc_status ecc_compute_batch(ecc_plan_t plan, int32_t n, const ecc_image *host_d
  *   lo, hi, complex_mode as in ecc_plan_desc; hi - lo + 1 must be <= 65536
  *   flags                ECC_FLAG_NO_RANGE_CHECK and ECC_FLAG_KERNEL_DIRECT honoured
  * Calls no cudaMalloc, cudaFree or allocating library routine.  The first
- * call on a device looks the scratch array up and clears it (set-up), so it
- * should come before any stream capture.  Each call clears what must start
+ * call on a device looks the scratch array up, clears it, and has the CUDA
+ * runtime load every kernel this call may launch (CUDA loads modules lazily
+ * by default, and loading one can take device memory): make that first
+ * call at start-up, before any memory pool reserves the device's memory and
+ * before any stream capture, or run with CUDA_MODULE_LOADING=EAGER.  A 3D
+ * image whose row pitch is not a multiple of 16 bytes takes the
+ * one-thread-per-voxel kernel here (same result; ecc_compute takes a faster
+ * path from its plan workspace, about 13x faster at 500^3 uint8).  Each call clears what must start
  * at zero; all calls on a device share the array, so calls whose work
  * overlaps on the GPU (other streams, other host threads) race and corrupt
  * each other's results.  Synchronous: returns after the work on `stream`

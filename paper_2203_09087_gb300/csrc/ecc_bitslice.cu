@@ -248,6 +248,20 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn()
     return fn;
 }
 
+// Loads (under lazy module loading) every 2D kernel a plan-free call can launch.
+cudaError_t preload_bs2d()
+{
+    const void *fns[] = {
+        (const void *)bs2d_kernel<unsigned char, false, 2>, (const void *)bs2d_kernel<unsigned char, true, 2>,
+        (const void *)bs2d_kernel<unsigned short, false, 2>, (const void *)bs2d_kernel<unsigned short, true, 2>};
+    cudaFuncAttributes fa;
+    for (const void *f : fns) {
+        const cudaError_t e = cudaFuncGetAttributes(&fa, f);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 bool bitslice_supported(const Geom &g)
 {
     if (g.esize != 1 && g.esize != 2) return false;

@@ -514,6 +514,32 @@ cudaError_t launch_w(const Geom &g, int64_t zb, int64_t ze, const HistDst &h, in
 
 }  // namespace
 
+// Loads (under lazy module loading) every 3D kernel a plan-free call with the
+// default tile can launch.
+cudaError_t preload_bs3d()
+{
+    const void *fns[] = {
+        (const void *)bs3_kernel<unsigned char, 4, false, false, true, false>,
+        (const void *)bs3_kernel<unsigned char, 4, true, false, true, false>,
+        (const void *)bs3_kernel<unsigned char, 4, false, true, true, false>,
+        (const void *)bs3_kernel<unsigned char, 4, true, true, true, false>,
+        (const void *)bs3_kernel<unsigned short, 4, false, false, true, false>,
+        (const void *)bs3_kernel<unsigned short, 4, true, false, true, false>,
+        (const void *)bs3_kernel<unsigned short, 4, false, true, true, false>,
+        (const void *)bs3_kernel<unsigned short, 4, true, true, true, false>,
+        (const void *)bs3_kernel<unsigned short, 4, false, false, false, false>,
+        (const void *)bs3_kernel<unsigned short, 4, true, false, false, false>,
+        (const void *)bs3_kernel<unsigned short, 4, false, true, false, false>,
+        (const void *)bs3_kernel<unsigned short, 4, true, true, false, false>,
+    };
+    cudaFuncAttributes fa;
+    for (const void *f : fns) {
+        const cudaError_t e = cudaFuncGetAttributes(&fa, f);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 // tune: warps per CTA (4 or 8); anything else picks 4.
 cudaError_t launch_bs3d(const Geom &g, int64_t zb, int64_t ze, const HistDst &h, int mode, bool range_check,
                         unsigned int *status, unsigned int *sched, int num_sms, int tune, cudaStream_t s,

@@ -257,6 +257,22 @@ cudaError_t launch_typed(const DirectArgs &a0, int num_sms, cudaStream_t s)
 
 }  // namespace
 
+// Loads (under lazy module loading) every one-thread-per-voxel kernel.
+cudaError_t preload_direct()
+{
+    const void *fns[] = {
+        (const void *)direct3d_kernel<unsigned char, false>, (const void *)direct3d_kernel<unsigned char, true>,
+        (const void *)direct3d_kernel<unsigned short, false>, (const void *)direct3d_kernel<unsigned short, true>,
+        (const void *)direct2d_kernel<unsigned char, false>, (const void *)direct2d_kernel<unsigned char, true>,
+        (const void *)direct2d_kernel<unsigned short, false>, (const void *)direct2d_kernel<unsigned short, true>};
+    cudaFuncAttributes fa;
+    for (const void *f : fns) {
+        const cudaError_t e = cudaFuncGetAttributes(&fa, f);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 cudaError_t launch_direct(const Geom &g, int64_t outer_begin, int64_t outer_end, const HistDst &h,
                           int complex_mode, bool range_check, unsigned int *status, int num_sms,
                           cudaStream_t s)

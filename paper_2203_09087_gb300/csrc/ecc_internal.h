@@ -108,6 +108,14 @@ cudaError_t launch_bs3d(const Geom &g, int64_t zb, int64_t ze, const HistDst &h,
                         unsigned int *status, unsigned int *sched, int num_sms, int tune, cudaStream_t s,
                         FusedScan *fs);
 
+// Force the loading of the kernels a plan-free call may launch (CUDA loads
+// modules lazily by default: a kernel's module, with its __device__ data, is
+// loaded at its first use unless something asks for it earlier).
+cudaError_t preload_bs3d();
+cudaError_t preload_bs2d();
+cudaError_t preload_direct();
+cudaError_t preload_scan();
+
 // Segmented inclusive scan of n_seg * nbins int64 values (segment i =
 // elements [i*nbins, (i+1)*nbins)).  Reads acc, writes ecc (and vcec if not
 // null), and zeroes acc for the next call.

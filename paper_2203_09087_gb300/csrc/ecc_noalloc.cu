@@ -14,8 +14,19 @@
 // The same stencil and scan kernels as ecc_compute run on it; only the
 // scratch pointer differs.  In host code the array's name is not a device
 // address, so the first call on each device looks its address up with
-// cudaGetSymbolAddress (with that device current) and clears it; that first
-// call therefore does set-up work and should come before any stream capture.
+// cudaGetSymbolAddress (with that device current), clears it, and makes the
+// CUDA runtime load every kernel this entry point may launch: CUDA loads the
+// library's modules lazily, at a kernel's first use, and loading a module can
+// take device memory.  The first call on each device therefore does set-up
+// work and belongs at start-up, before any memory pool reserves the device's
+// memory and before any stream capture (or the process runs with
+// CUDA_MODULE_LOADING=EAGER).
+//
+// A 3D image whose rows the TMA cannot address (row pitch not a multiple of
+// 16 bytes) takes the one-thread-per-voxel kernel here, where ecc_compute
+// walks it with the batch kernel from its plan workspace; the result is the
+// same, about 13x slower (500^3 uint8: 1.98 ms against 0.15 ms).
+//
 // Every call on a device shares the array: each call clears the parts that
 // must start at zero before using them, and calls whose work overlaps on the
 // GPU (different streams, or host threads racing) corrupt each other's
@@ -50,8 +61,11 @@ static __device__ __align__(256) unsigned long long g_noalloc_scratch[kScratchWo
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 unsigned long long *g_ptr[kMaxDevices] = {};
+int g_sms[kMaxDevices] = {};
 
-ecc_status scratch_for_current_device(unsigned long long **out)
+// The scratch array's device address and the SM count of the current device;
+// the first call per device also clears the array and loads the kernels.
+ecc_status scratch_for_current_device(unsigned long long **out, int *sms)
 {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -67,9 +81,17 @@ ecc_status scratch_for_current_device(unsigned long long **out)
         if (e != cudaSuccess) return cuda_fail(e, "ecc_compute_noalloc: cudaGetSymbolAddress");
         e = clear_device_now(p, sizeof(g_noalloc_scratch));
         if (e != cudaSuccess) return cuda_fail(e, "ecc_compute_noalloc: scratch clear");
+        if ((e = preload_bs3d()) != cudaSuccess || (e = preload_bs2d()) != cudaSuccess ||
+            (e = preload_direct()) != cudaSuccess || (e = preload_scan()) != cudaSuccess)
+            return cuda_fail(e, "ecc_compute_noalloc: kernel loading");
+        int n = 0;
+        e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return cuda_fail(e, "ecc_compute_noalloc: device query");
+        g_sms[dev] = n;
         g_ptr[dev] = static_cast<unsigned long long *>(p);
     }
     *out = g_ptr[dev];
+    *sms = g_sms[dev];
     return ECC_OK;
 }
 
@@ -103,7 +125,8 @@ extern "C" ecc_status ecc_compute_noalloc(const ecc_image *img, int32_t lo, int3
     ecc_status st = image_geom(img, 0, 0, &g, nullptr, false);
     if (st != ECC_OK) return st;
     unsigned long long *base = nullptr;
-    st = scratch_for_current_device(&base);
+    int sms = 0;
+    st = scratch_for_current_device(&base, &sms);
     if (st != ECC_OK) return st;
 
     unsigned long long *acc = base;
@@ -119,10 +142,6 @@ extern "C" ecc_status ecc_compute_noalloc(const ecc_image *img, int32_t lo, int3
     if (e == cudaSuccess) e = cudaMemsetAsync(ctl, 0, sizeof(unsigned long long) * (kCtlWords + kStatWords), s);
     if (e != cudaSuccess) return cuda_fail(e, "ecc_compute_noalloc: clear");
 
-    int sms = 0, dev = 0;
-    cudaGetDevice(&dev);
-    e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (e != cudaSuccess) return cuda_fail(e, "ecc_compute_noalloc: device query");
     const bool range = !(flags & ECC_FLAG_NO_RANGE_CHECK);
     HistDst h{acc, lo, (int32_t)nbins};
     const int64_t outer = g.ndim == 3 ? g.nz : g.ny;

@@ -213,6 +213,13 @@ int64_t scan_tiles(int64_t n_seg, int32_t nbins)
     return (n + kScanTile - 1) / kScanTile;
 }
 
+// Loads (under lazy module loading) the scan kernel.
+cudaError_t preload_scan()
+{
+    cudaFuncAttributes fa;
+    return cudaFuncGetAttributes(&fa, (const void *)scan_kernel);
+}
+
 cudaError_t launch_scan(unsigned long long *acc, long long *ecc, long long *vcec, int64_t n_seg,
                         int32_t nbins, const ScanWs &ws, unsigned int *status, cudaStream_t s)
 {

@@ -67,3 +67,13 @@ def test_whole_job_value_counts_all_replicas():
     assert bench.whole_job_gvox_s(1 << 27, 4, 4, 0.5) == pytest.approx(4 * one)
     assert one == pytest.approx((1 << 27) * 4 / 0.5 / 1e9)
     assert json.dumps(one)
+
+
+def test_gpus_flag_must_match_the_ranks():
+    """--gpus N under a launcher that started a different number of ranks is
+    refused (no rank silently runs a one-GPU job)."""
+    env = dict(os.environ, WORLD_SIZE="1", RANK="0", LOCAL_RANK="0")
+    r = subprocess.run([sys.executable, str(ROOT / "bench.py"), "--gpus", "2", "--steps", "1"], env=env,
+                       capture_output=True, text=True, timeout=120)
+    assert r.returncode == 2
+    assert "WORLD_SIZE=1" in r.stderr

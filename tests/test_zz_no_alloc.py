@@ -5,9 +5,9 @@ pipeline whose device budget is fixed at start-up, or code running inside
 another framework's memory pool.  ecc_compute_noalloc serves them from one
 fixed scratch array of the library instead of a plan's cudaMalloc'd
 workspace.  These tests call it through the C ABI and check it against the
-plan-based ecc_compute on the same images, exactly (integer results), on two
-calls in a row, so a second call cannot inherit the first call's scratch
-contents unnoticed.
+plan-based ecc_compute and against the CPU oracle on the same images, exactly
+(integer results), on two calls in a row, so a second call cannot inherit the
+first call's scratch contents unnoticed.
 
 The file name sorts last so that a run stopping at the first failure has
 already run every other test; it also passes alone in a fresh process.
@@ -16,6 +16,8 @@ import ctypes
 
 import numpy as np
 import pytest
+
+import oracle
 
 torch = pytest.importorskip("torch")
 
@@ -79,6 +81,34 @@ def test_two_calls_in_a_row_match_ecc_compute(kind, mode):
     assert _noalloc_cabi(tb, lo, hi, mode, out_b) == 0, _ecc().ecc_last_error()
     assert np.array_equal(out_a.cpu().numpy(), _with_plan(ta, lo, hi, mode))
     assert np.array_equal(out_b.cpu().numpy(), _with_plan(tb, lo, hi, mode))
+    om = oracle.VERTEX if mode == 0 else oracle.TOPCELL
+    assert np.array_equal(out_a.cpu().numpy(), oracle.ecc(a, lo, hi, om))
+    assert np.array_equal(out_b.cpu().numpy(), oracle.ecc(b, lo, hi, om))
+
+
+def test_wrapper_with_vcec_on_a_side_stream():
+    """The Python wrapper, a VCEC output and a non-default stream: ECC and
+    VCEC equal the plan path's and the oracle's."""
+    ecc = _ecc()
+    rng = np.random.default_rng(23)
+    img = rng.integers(0, 256, size=(18, 45, 80), dtype=np.uint8)
+    t = torch.from_numpy(img).cuda()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        out = torch.full((256,), -1, dtype=torch.int64, device="cuda")
+        vcec = torch.full((256,), -1, dtype=torch.int64, device="cuda")
+        ecc.ecc_compute_noalloc(t, 0, 255, 0, out=out, vcec_out=vcec, stream=side)
+    side.synchronize()
+    plan = ecc.ecc_plan("u8", 0, 255, max_voxels=img.size)
+    p_vcec = torch.empty(256, dtype=torch.int64, device="cuda")
+    p_out = ecc.ecc_compute(plan, t, vcec_out=p_vcec)
+    ecc.ecc_status_get(plan)
+    assert np.array_equal(out.cpu().numpy(), p_out.cpu().numpy())
+    assert np.array_equal(vcec.cpu().numpy(), p_vcec.cpu().numpy())
+    want_v = oracle.vcec(img, 0, 255)
+    assert np.array_equal(vcec.cpu().numpy(), want_v)
+    assert np.array_equal(out.cpu().numpy(), np.cumsum(want_v))
 
 
 def test_rejects_bad_requests_with_a_clear_error():
