@@ -6,10 +6,12 @@
 // GB300:
 //
 //  * Bit-slicing (ecc_walk3.cuh).  A lane holds a window of 32 voxels of one
-//    row as bit planes; lanes are 32 consecutive rows (lanes 0 and 31 the y
-//    halo), windows overlap by one voxel on each side (30 outputs), so a
-//    warp owns a 30x30 column of the volume and walks it along z.  Each of
-//    the 13 neighbour directions is compared once per voxel pair.
+//    row as bit planes; lanes are 32 consecutive rows.  Windows and lane
+//    rows overlap their neighbours by one voxel on each side, so an inner
+//    warp owns a 30x30 column of the volume (31 along an axis where its tile
+//    touches the image edge: the missing neighbour there needs no halo) and
+//    walks it along z.  Each of the 13 neighbour directions is compared once
+//    per voxel pair.
 //  * Independent warps.  Each warp streams its own column through a private
 //    ring of S shared-memory stages, one TMA copy (cp.async.bulk.tensor.3d)
 //    of D planes x 32 rows x 48 (uint8) or 80 (uint16) bytes per stage,
@@ -48,8 +50,6 @@ namespace ecc {
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn();  // ecc_bitslice.cu
 
 namespace {
-
-constexpr int kOut = 30;  // output voxels per window along x, output rows per warp along y
 
 // Ring shape per element type and warps per CTA: D planes per stage (one TMA
 // copy), S stages per warp.  A stage is refilled once the step after its
@@ -199,9 +199,10 @@ __global__ void __launch_bounds__(NWARP * 32, bs3_min_blocks<T, NWARP>())
             if (c.item >= 0) {
                 const int xi = c.item % a.ntx, r = c.item / a.ntx;
                 const int yt = r % a.nty, zc = r / a.nty;
-                const int xw = xi * kOut - 1;
-                c.bx = xw >= 0 ? xw / ALIGN_EL * ALIGN_EL : -ALIGN_EL;
-                c.y0 = yt * kOut - 1;
+                int xw, ylo, yhi;
+                walk3::tile_span(a.nx, a.ntx, xi, xw, ylo, yhi);
+                c.bx = xw / ALIGN_EL * ALIGN_EL;
+                walk3::tile_span(a.ny, a.nty, yt, c.y0, ylo, yhi);
                 const int zb = a.z_begin + zc * a.zchunk;
                 const int ze = zb + a.zchunk < a.z_end ? zb + a.zchunk : a.z_end;
                 c.z0 = zb - 1;
@@ -270,17 +271,26 @@ __global__ void __launch_bounds__(NWARP * 32, bs3_min_blocks<T, NWARP>())
         }
         const int xi = item % a.ntx, rr = item / a.ntx;
         const int yt = rr % a.nty, zc = rr / a.nty;
-        const int xw = xi * kOut - 1;  // voxel of window bit 0
-        const int bx = xw >= 0 ? xw / ALIGN_EL * ALIGN_EL : -ALIGN_EL;
+        int xw, xlo, xhi, y0, ylo, yhi;  // window bit 0 is voxel xw, lane 0 is row y0
+        walk3::tile_span(a.nx, a.ntx, xi, xw, xlo, xhi);
+        walk3::tile_span(a.ny, a.nty, yt, y0, ylo, yhi);
+        const int bx = xw / ALIGN_EL * ALIGN_EL;
         const int off = (xw - bx) * ES;
-        const int y = yt * kOut - 1 + lane;
+        const int y = y0 + lane;
         const int zb = a.z_begin + zc * a.zchunk;
         const int ze = zb + a.zchunk < a.z_end ? zb + a.zchunk : a.z_end;
         const int n = ze - zb + 2;  // planes zb-1 .. ze
         const uint32_t xex = walk::x_exist_mask(xw, a.nx);
-        const bool lane_out = lane >= 1 && lane <= kOut && y < a.ny;
-        const uint32_t out_x = lane_out ? (xex & 0x7ffffffeu) : 0u;
-        const uint32_t e_row = (y >= 0 && y < a.ny) ? ~xex : 0xffffffffu;
+        const bool lane_out = lane >= ylo && lane < yhi && y < a.ny;
+        const uint32_t xmask = (xhi == 32 ? 0xffffffffu : (1u << xhi) - 1u) & ~((1u << xlo) - 1u);
+        const uint32_t out_x = lane_out ? (xex & xmask) : 0u;
+        const uint32_t e_row = y < a.ny ? ~xex : 0xffffffffu;
+        walk3::Fill fill;
+        fill.xl = xw == 0 ? 1u : 0u;
+        fill.xr = xw + 32 >= a.nx ? 0x80000000u : 0u;
+        fill.yt = lane == 0 && y0 == 0;
+        fill.yb = lane == 31 && y0 + 32 >= a.ny;
+        fill.edge = xw == 0 || xw + 32 >= a.nx || y0 == 0 || y0 + 32 >= a.ny;
         int vals = 0;  // smem offset of the emitted plane's window in this lane's row
         auto emit = [&](uint32_t m, const uint32_t *T) {
             walk3::emit3<TOP>(
@@ -316,7 +326,7 @@ __global__ void __launch_bounds__(NWARP * 32, bs3_min_blocks<T, NWARP>())
             const int row = ring + c_slot * STAGE + lane * ROWB + d * PLANE;
             load(rB, row, zb - 1 + p);
             if (p > 0) {
-                wk.step(rA, rB, p >= 2, out_x, mu, emit);
+                wk.step(rA, rB, p >= 2, out_x, fill, mu, emit);
                 if (d == 0) {
                     __syncwarp();
                     issue();  // the previous stage (plane p-1) is free
@@ -393,8 +403,8 @@ cudaError_t launch_t(const Geom &g, int64_t zb, int64_t ze, const HistDst &h, bo
     a.nz = (int32_t)g.nz;
     a.z_begin = (int32_t)zb;
     a.z_end = (int32_t)ze;
-    a.ntx = (int32_t)((g.nx + kOut - 1) / kOut);
-    a.nty = (int32_t)((g.ny + kOut - 1) / kOut);
+    a.ntx = walk3::tiles_of((int)g.nx);
+    a.nty = walk3::tiles_of((int)g.ny);
     a.h = h;
     a.check_range = NARROW && range_check;
     a.lo_bits = (uint32_t)h.lo;

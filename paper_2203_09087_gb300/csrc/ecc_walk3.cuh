@@ -67,6 +67,51 @@ __device__ __forceinline__ void emit3(uint32_t m, const uint32_t *T, ValAt &&val
     }
 }
 
+// Tiles along x (windows) and y (lane rows) of n positions.  A tile holds 32
+// consecutive positions from `start`; its outputs are [lo, hi).  Positions
+// next to an output must be in the tile -- except beyond the image edge,
+// where the neighbour is missing and its comparisons are known (see Fill) --
+// so the first tile outputs positions 0..30 (31), inner tiles 30 (their
+// positions 1..30), the last tile up to 31 (positions up to 31), and a single
+// tile (n <= 32) all n.
+__host__ __device__ __forceinline__ int tiles_of(int n)
+{
+    return n <= 32 ? 1 : 2 + (n - 62 > 0 ? (n - 62 + 29) / 30 : 0);
+}
+
+__host__ __device__ __forceinline__ void tile_span(int n, int nt, int t, int &start, int &lo, int &hi)
+{
+    if (nt == 1) {
+        start = 0;
+        lo = 0;
+        hi = n < 32 ? n : 32;
+    } else if (t == 0) {
+        start = 0;
+        lo = 0;
+        hi = 31;
+    } else if (t < nt - 1) {
+        start = 30 * t;
+        lo = 1;
+        hi = 31;
+    } else {
+        start = n - 32;
+        lo = 30 * (nt - 1) + 1 - start;
+        hi = 32;
+    }
+}
+
+// What the walk knows about neighbours beyond the image edge of its tile.
+// A comparison with a missing voxel has a fixed outcome: in the vertex
+// complex a missing voxel beats every real one (it compares as 2^K), in the
+// top-cell complex it loses (the voxel owns the boundary cell).  Those
+// outcomes are shifted in where a window's bit 0 or 31, or a warp's lane 0
+// or 31, takes a neighbour from outside the tile.
+struct Fill {
+    uint32_t xl, xr;    // 1 / 0x80000000 when the voxel left of bit 0 / right of bit 31 is missing, else 0
+    bool yt, yb;        // this lane is lane 0 and row y-1 is missing / lane 31 and row y+1 is missing
+    bool edge;          // any of these for the warp (warp-uniform)
+};
+
 // The walk: step(a, b) compares plane z (row a) with plane z+1 (row b) and
 // the in-plane pairs of plane z+1, and emits plane z.  State between steps:
 // the wins of plane z+1 over plane z and over its in-plane neighbours that
@@ -97,8 +142,8 @@ struct Walk {
     // emit(mask, T): output voxels of plane z with a nonzero count (mask
     // already restricted to out_x).  Warp-collective.
     template <class Emit>
-    __device__ __forceinline__ void step(const Row<K> &a, const Row<K> &b, bool emit_z, uint32_t out_x, const Mul &mu,
-                                         Emit &&emit)
+    __device__ __forceinline__ void step(const Row<K> &a, const Row<K> &b, bool emit_z, uint32_t out_x, const Fill &fl,
+                                         const Mul &mu, Emit &&emit)
     {
         // R0[d] = A(y)[x] vs B(y)[x+d-1]; G[d] = A(y-1)[x] vs B(y)[x+d-1];
         // K2[d] = A(y+1)[x] vs B(y)[x+d-1]; E = B(y)[x-1] vs B(y)[x];
@@ -142,13 +187,46 @@ struct Walk {
         plane(0, true);
 #pragma unroll
         for (int k = 1; k < K; ++k) plane(k, false);
-        if (__any_sync(0xffffffffu, (a.P[K] | b.P[K]) != 0u)) plane(K, false);
+        if (fl.edge || __any_sync(0xffffffffu, (a.P[K] | b.P[K]) != 0u)) {
+            // the existence planes, with missing neighbours shifted and
+            // shuffled in beyond the image edge
+            const uint32_t bP = b.P[K], aP = a.P[K];
+            const uint32_t bm = bP * mu.two + fl.xl, bp = umulhi(bP, mu.half) + fl.xr;
+            uint32_t bU = walk::from_next_lane(bP), aU = walk::from_next_lane(aP), d = walk::from_prev_lane(aP);
+            if (fl.yb) bU = aU = ~0u;
+            if (fl.yt) d = ~0u;
+            R0[0] = cmpk<TOP>(aP, bm, R0[0]);
+            R0[1] = cmpk<TOP>(aP, bP, R0[1]);
+            R0[2] = cmpk<TOP>(aP, bp, R0[2]);
+            G[0] = cmpk<TOP>(d, bm, G[0]);
+            G[1] = cmpk<TOP>(d, bP, G[1]);
+            G[2] = cmpk<TOP>(d, bp, G[2]);
+            K2[0] = cmpk<TOP>(aU, bm, K2[0]);
+            K2[1] = cmpk<TOP>(aU, bP, K2[1]);
+            K2[2] = cmpk<TOP>(aU, bp, K2[2]);
+            E = cmpk<TOP>(bm, bP, E);
+            F[0] = cmpk<TOP>(bp, bU, F[0]);
+            F[1] = cmpk<TOP>(bP, bU, F[1]);
+            F[2] = cmpk<TOP>(bm, bU, F[2]);
+        }
         uint32_t Gu[3], K2d[3], Fd[3];
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
             Gu[d] = walk::from_next_lane(G[d]);    // lane y+1's G: A(y) vs B(y+1)
             K2d[d] = walk::from_prev_lane(K2[d]);  // lane y-1's K2: A(y) vs B(y-1)
             Fd[d] = walk::from_prev_lane(F[d]);    // lane y-1's F
+        }
+        if (fl.edge) {
+            // rows beyond the image edge: A(y) vs missing B(y+1) or B(y-1),
+            // missing B(y-1) vs B(y)
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                if (fl.yb) Gu[d] = TOP ? ~0u : 0u;
+                if (fl.yt) {
+                    K2d[d] = TOP ? ~0u : 0u;
+                    Fd[d] = TOP ? 0u : ~0u;
+                }
+            }
         }
         if (emit_z) {
             uint32_t up[3][3];
@@ -159,24 +237,29 @@ struct Walk {
                 up[0][d] = K2d[d];
             }
             uint32_t T[4];
-            const uint32_t m = kappa3w(up, nW, sE, shr1(sE, mu), sF, sD, out_x, T);
+            const uint32_t m = kappa3w(up, nW, sE, umulhi(sE, mu.half) + (TOP ? fl.xr : 0u), sF, sD, out_x, T);
             emit(m, T);
         }
         // the state of plane z+1: its wins over plane z (a neighbour earlier
         // in memory wins ties, so these are negations) and in-plane
-        nW[1][0] = at_offset<-1>(R0[2], mu);
+        // (shifts bring in a missing neighbour's outcome beyond the image
+        // edge: the earlier voxel missing, it beats in the vertex complex;
+        // the later one missing, it is beaten in the top-cell complex)
+        const uint32_t el = TOP ? 0u : fl.xl, er = TOP ? 0u : fl.xr;  // earlier operand missing
+        const uint32_t ll = TOP ? fl.xl : 0u, lr = TOP ? fl.xr : 0u;  // later operand missing
+        nW[1][0] = R0[2] * mu.two + el;
         nW[1][1] = R0[1];
-        nW[1][2] = at_offset<+1>(R0[0], mu);
-        nW[2][0] = at_offset<-1>(K2[2], mu);
+        nW[1][2] = umulhi(R0[0], mu.half) + er;
+        nW[2][0] = K2[2] * mu.two + el;
         nW[2][1] = K2[1];
-        nW[2][2] = at_offset<+1>(K2[0], mu);
-        nW[0][0] = at_offset<-1>(G[2], mu);
+        nW[2][2] = umulhi(K2[0], mu.half) + er;
+        nW[0][0] = G[2] * mu.two + el;
         nW[0][1] = G[1];
-        nW[0][2] = at_offset<+1>(G[0], mu);
+        nW[0][2] = umulhi(G[0], mu.half) + er;
         sE = E;
-        sF[0] = at_offset<-1>(F[0], mu);
+        sF[0] = F[0] * mu.two + ll;
         sF[1] = F[1];
-        sF[2] = at_offset<+1>(F[2], mu);
+        sF[2] = umulhi(F[2], mu.half) + lr;
         sD[0] = Fd[0];
         sD[1] = Fd[1];
         sD[2] = Fd[2];
