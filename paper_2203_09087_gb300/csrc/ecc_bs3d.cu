@@ -61,8 +61,8 @@ struct C3 {
     static constexpr int WORDS = 8 * ES;                // 32-bit words of a 32-voxel window
     static constexpr int CHUNKS = 2 * ES + 1;           // 16-byte loads covering a window at any offset
     static constexpr int ROWB = 16 * CHUNKS;            // bytes of a staged row (odd number of 16-byte units)
-    static constexpr int D = NWARP == 8 ? 1 : 2;
-    static constexpr int S = NWARP == 8 ? 4 : 3;
+    static constexpr int D = ES == 1 ? 2 : 1;
+    static constexpr int S = ES == 1 ? 3 : 4;
     static constexpr int PLANE = 32 * ROWB;
     static constexpr int STAGE = D * PLANE;             // multiple of 128 bytes
 };
@@ -112,18 +112,19 @@ __device__ __forceinline__ void load_window(const unsigned char *row, int off, u
         v[4 * c + 3] = q.w;
     }
     uint32_t r[C::WORDS];
-    const int wsh = (off & 3) * 8;
-    const uint32_t m = bs::kPow2[(32 - wsh) & 31];  // unused when wsh == 0
-    // word offset (warp-uniform) by a switch; the byte shift as two
-    // multiplies (disjoint bits: the add is an or)
+    const uint32_t sh = (uint32_t)(off & 3);
+    // the byte shift as one byte permute per word: bytes sh..sh+3 of the pair
+    // (a right shift would cost the same ALU slot, and a multiply pair more)
+    const uint32_t sel = sh | ((sh + 1) << 4) | ((sh + 2) << 8) | ((sh + 3) << 12);
+    // word offset (warp-uniform) by a switch
     switch (off >> 2) {
 #define ECC_WIN(W)                                                                \
     case W:                                                                       \
-        if (wsh == 0) {                                                           \
+        if (sh == 0) {                                                            \
             _Pragma("unroll") for (int i = 0; i < C::WORDS; ++i) r[i] = v[i + W]; \
         } else {                                                                  \
             _Pragma("unroll") for (int i = 0; i < C::WORDS; ++i) r[i] =           \
-                v[i + W + 1] * m + __umulhi(v[i + W], m);                         \
+                __byte_perm(v[i + W], v[i + W + 1], sel);                         \
         }                                                                         \
         break;
         ECC_WIN(0)
@@ -145,13 +146,14 @@ constexpr int bs3_min_blocks()
 }
 
 // The TMA side of one warp's ring, kept in shared memory and used by lane 0
-// only (no registers in the other lanes).
-struct LoadCursor {
-    int item;      // item being loaded; -1 once the work list is exhausted, -2 before the first
+// only (no registers in the other lanes): what changes per stage in one
+// 16-byte word, the item's box origin in another.
+struct __align__(16) LoadCursor {
     int st, nst;   // next stage of the item, and its number of stages
-    int bx, y0, z0;
     int slot;      // ring slot of the next stage
     int issued;    // stages issued so far
+    int item;      // item being loaded; -1 once the work list is exhausted, -2 before the first
+    int bx, y0, z0;
 };
 
 template <typename T, int NWARP, bool TOP, bool NARROW, bool SMEM, bool COUNT>
@@ -178,7 +180,7 @@ __global__ void __launch_bounds__(NWARP * 32, bs3_min_blocks<T, NWARP>())
     if (lane == 0) {
         for (int s = 0; s < S; ++s) mbar_init(&full[s], 1);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        s_cur[warp] = LoadCursor{-2, 0, 0, 0, 0, 0, 0, 0};
+        s_cur[warp] = LoadCursor{0, 0, 0, 0, -2, 0, 0, 0};
     }
     __syncthreads();
 
@@ -190,7 +192,9 @@ __global__ void __launch_bounds__(NWARP * 32, bs3_min_blocks<T, NWARP>())
     // list is exhausted, a stage is a plain arrival tagged -1.
     auto issue = [&]() {
         if (lane != 0) return;
-        LoadCursor c = s_cur[warp];
+        LoadCursor c;
+        *reinterpret_cast<int4 *>(&c.st) = *reinterpret_cast<const int4 *>(&s_cur[warp].st);
+        *reinterpret_cast<int4 *>(&c.item) = *reinterpret_cast<const int4 *>(&s_cur[warp].item);
         if (c.st >= c.nst) {
             if (c.item != -1) {
                 const unsigned int it = atomicAdd(a.sched, 1u);
@@ -211,6 +215,7 @@ __global__ void __launch_bounds__(NWARP * 32, bs3_min_blocks<T, NWARP>())
                 c.nst = 0;
             }
             c.st = 0;
+            *reinterpret_cast<int4 *>(&s_cur[warp].item) = *reinterpret_cast<const int4 *>(&c.item);
         }
         tag[c.slot] = c.item;
         if (c.item >= 0) {
@@ -222,7 +227,7 @@ __global__ void __launch_bounds__(NWARP * 32, bs3_min_blocks<T, NWARP>())
         ++c.st;
         ++c.issued;
         if (++c.slot == S) c.slot = 0;
-        s_cur[warp] = c;
+        *reinterpret_cast<int4 *>(&s_cur[warp].st) = *reinterpret_cast<const int4 *>(&c.st);
     };
 
     // ------------------------------------------------ walk
@@ -257,6 +262,17 @@ __global__ void __launch_bounds__(NWARP * 32, bs3_min_blocks<T, NWARP>())
             atomicAdd(&hist[bin], k);
         else
             atomicAdd(a.h.acc + bin, (unsigned long long)(long long)k);
+    };
+    // the common single +-1 add of a lane, predicated instead of branched
+    // (full range and shared bins only: nothing to check)
+    auto add_if = [&](bool p, int v, int k) {
+        if constexpr (SMEM && !NARROW && !COUNT) {
+            const uint32_t addr = sync::smem_u32(hist + (v - a.h.lo));
+            asm volatile("{\n .reg .pred q;\n setp.ne.u32 q, %0, 0;\n @q red.shared.add.s32 [%1], %2;\n}\n"
+                         ::"r"((uint32_t)p), "r"(addr), "r"(k) : "memory");
+        } else {
+            if (p) add(v, k);
+        }
     };
 
     for (int i = 0; i < S; ++i) issue();
@@ -299,7 +315,7 @@ __global__ void __launch_bounds__(NWARP * 32, bs3_min_blocks<T, NWARP>())
                     return ES == 1 ? (int)smem[vals + i]
                                    : (int)reinterpret_cast<const unsigned short *>(smem + vals)[i];
                 },
-                add);
+                add, add_if);
         };
         // load plane z (this lane's row at smem offset `row`) into r
         auto load = [&](walk3::Row<K> &r, int row, int z) {
@@ -529,18 +545,18 @@ cudaError_t launch_w(const Geom &g, int64_t zb, int64_t ze, const HistDst &h, in
 cudaError_t preload_bs3d()
 {
     const void *fns[] = {
-        (const void *)bs3_kernel<unsigned char, 4, false, false, true, false>,
-        (const void *)bs3_kernel<unsigned char, 4, true, false, true, false>,
-        (const void *)bs3_kernel<unsigned char, 4, false, true, true, false>,
-        (const void *)bs3_kernel<unsigned char, 4, true, true, true, false>,
-        (const void *)bs3_kernel<unsigned short, 4, false, false, true, false>,
-        (const void *)bs3_kernel<unsigned short, 4, true, false, true, false>,
-        (const void *)bs3_kernel<unsigned short, 4, false, true, true, false>,
-        (const void *)bs3_kernel<unsigned short, 4, true, true, true, false>,
-        (const void *)bs3_kernel<unsigned short, 4, false, false, false, false>,
-        (const void *)bs3_kernel<unsigned short, 4, true, false, false, false>,
-        (const void *)bs3_kernel<unsigned short, 4, false, true, false, false>,
-        (const void *)bs3_kernel<unsigned short, 4, true, true, false, false>,
+        (const void *)bs3_kernel<unsigned char, 8, false, false, true, false>,
+        (const void *)bs3_kernel<unsigned char, 8, true, false, true, false>,
+        (const void *)bs3_kernel<unsigned char, 8, false, true, true, false>,
+        (const void *)bs3_kernel<unsigned char, 8, true, true, true, false>,
+        (const void *)bs3_kernel<unsigned short, 8, false, false, true, false>,
+        (const void *)bs3_kernel<unsigned short, 8, true, false, true, false>,
+        (const void *)bs3_kernel<unsigned short, 8, false, true, true, false>,
+        (const void *)bs3_kernel<unsigned short, 8, true, true, true, false>,
+        (const void *)bs3_kernel<unsigned short, 8, false, false, false, false>,
+        (const void *)bs3_kernel<unsigned short, 8, true, false, false, false>,
+        (const void *)bs3_kernel<unsigned short, 8, false, true, false, false>,
+        (const void *)bs3_kernel<unsigned short, 8, true, true, false, false>,
     };
     cudaFuncAttributes fa;
     for (const void *f : fns) {
@@ -550,17 +566,17 @@ cudaError_t preload_bs3d()
     return cudaSuccess;
 }
 
-// tune: warps per CTA (4 or 8); anything else picks 4.
+// tune: warps per CTA (4 or 8); anything else picks 8.
 cudaError_t launch_bs3d(const Geom &g, int64_t zb, int64_t ze, const HistDst &h, int mode, bool range_check,
                         unsigned int *status, unsigned int *sched, int num_sms, int tune, cudaStream_t s,
                         FusedScan *fs)
 {
     if (g.nx > 2147483647 - 64 || g.ny > 2147483647 - 64 || g.nz > 2147483647 - 64) return cudaErrorNotSupported;
     if (g.esize == 1)
-        return tune == 8 ? launch_w<unsigned char, 8>(g, zb, ze, h, mode, range_check, status, sched, num_sms, s, fs)
-                         : launch_w<unsigned char, 4>(g, zb, ze, h, mode, range_check, status, sched, num_sms, s, fs);
-    return tune == 8 ? launch_w<unsigned short, 8>(g, zb, ze, h, mode, range_check, status, sched, num_sms, s, fs)
-                     : launch_w<unsigned short, 4>(g, zb, ze, h, mode, range_check, status, sched, num_sms, s, fs);
+        return tune == 4 ? launch_w<unsigned char, 4>(g, zb, ze, h, mode, range_check, status, sched, num_sms, s, fs)
+                         : launch_w<unsigned char, 8>(g, zb, ze, h, mode, range_check, status, sched, num_sms, s, fs);
+    return tune == 4 ? launch_w<unsigned short, 4>(g, zb, ze, h, mode, range_check, status, sched, num_sms, s, fs)
+                     : launch_w<unsigned short, 8>(g, zb, ze, h, mode, range_check, status, sched, num_sms, s, fs);
 }
 
 }  // namespace ecc

@@ -5,7 +5,7 @@
 // chooses
 //   * the 3D bit-sliced kernel's warps per CTA (4 or 8: warps sharing one
 //     shared histogram and one flush), timed in three interleaved rounds on
-//     a synthetic 512x512x256 volume, 4 kept unless 8 is at least 3 %
+//     a synthetic 512x512x256 volume, 8 kept unless 4 is at least 3 %
 //     faster;
 //   * the batched kernel's rows per 2D tile (16, 32, 64) and planes per 3D
 //     tile (8, 16, 32), timed on a synthetic uneven batch.
@@ -175,8 +175,9 @@ void ecc_plan_s::autotune()
                         s, 5);
                     best_of[ci] = ms < best_of[ci] ? ms : best_of[ci];
                 }
-            // 4 warps per CTA unless 8 is at least 3 % faster
-            c.a = best_of[1] < 0.97f * best_of[0] ? 8 : 4;
+            // 8 warps per CTA unless 4 is at least 3 % faster (8 measured
+            // 2-4 % faster at 512^3 uint8, equal at 1024^3 uint16)
+            c.a = best_of[0] < 0.97f * best_of[1] ? 4 : 8;
             cudaStreamSynchronize(s);
             cudaFree(buf);
         }
