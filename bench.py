@@ -327,6 +327,30 @@ def run_single_u16(args):
     return res
 
 
+def time_c3(reps=3):
+    """The 1024^3 uint16 volume alone: one checked call, then `reps` calls
+    timed with CUDA events (for profiler captures of the 16-bit kernel)."""
+    import torch
+
+    import paper_2203_09087_gb300 as ecc
+    import synth
+    vol = synth.config3_smooth_blobs_u16(device="cuda")
+    plan = ecc.ecc_plan("u16", 0, 65535, max_voxels=vol.numel())
+    out = torch.empty(65536, dtype=torch.int64, device="cuda")
+    ecc.ecc_compute(plan, vol, out)
+    ecc.ecc_status_get(plan)
+    assert int(out[-1].item()) == 1
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(reps):
+        ecc.ecc_compute(plan, vol, out)
+    e1.record()
+    e1.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    return {"workload": "1024^3 uint16 (C3 input), 65536 bins", "ms_per_call": ms,
+            "gvox_s": vol.numel() / ms / 1e6}
+
+
 def run_float_levels(args):
     """Float32 input at given thresholds (the paper's Gaussian random fields
     are float32 with 1024 values): a 512^3 float32 field smoothed with sigma
@@ -638,6 +662,8 @@ def main():
                     help="profiler runs: no one-second warm-up floor, no e2e and CPU legs")
     ap.add_argument("--only-4d", type=int, default=0, metavar="SIDE",
                     help="profiler runs: only the 4D case SIDE^4 uint8 (three calls after the checked one)")
+    ap.add_argument("--only-c3", action="store_true",
+                    help="profiler runs: only the 1024^3 uint16 volume (three calls after the checked one)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     ws_env = int(os.environ.get("WORLD_SIZE", "1"))
@@ -658,6 +684,9 @@ def main():
     if args.only_4d:
         import numpy as np
         print(json.dumps(time_4d(args.only_4d, np.uint8, 255, reps=3)))
+        return
+    if args.only_c3:
+        print(json.dumps(time_c3(reps=3)))
         return
 
     import numpy as np

@@ -46,8 +46,8 @@ struct Row {
 // from a valid index, only the add predicated), and the warp runs the
 // general loop only when some lane has more, or a larger count.
 // Warp-collective.
-template <bool TOP, class ValAt, class Add>
-__device__ __forceinline__ void emit3(uint32_t m, const uint32_t *T, ValAt &&val_at, Add &&add)
+template <bool TOP, class ValAt, class Add, class AddIf>
+__device__ __forceinline__ void emit3(uint32_t m, const uint32_t *T, ValAt &&val_at, Add &&add, AddIf &&add_if)
 {
     const uint32_t c = lop3<0x10u>(T[2], T[3], T[0]);  // T[2] & ~T[3] & ~T[0]: T = 4 or 6
     const uint32_t pm = m & c;
@@ -56,7 +56,7 @@ __device__ __forceinline__ void emit3(uint32_t m, const uint32_t *T, ValAt &&val
     const int i = 31 - __clz(first | 1u);
     const int v = val_at(i);
     const int k = (T[1] & first) ? 1 : -1;
-    if (first) add(v, TOP ? -k : k);
+    add_if(first != 0u, v, TOP ? -k : k);
     if (__any_sync(0xffffffffu, rest != 0u)) {
         while (rest) {
             const int j = __ffs(rest) - 1;

@@ -89,3 +89,74 @@ def test_paper_size_1024_square_grf():
     want, final = oracle.gaussian_pipeline(img, taps, levels.astype(np.float64), 12, "vertex", threads=16)
     assert np.array_equal(got, want)
     assert np.array_equal(t.cpu().numpy(), final)
+
+
+# ----------------------------------------------------------------------------
+# 2D images with at most 255 levels take one fused kernel per round (tile read
+# once: level search, bit-sliced cell count, both filter passes); the cases
+# below cover its tile edges, halo widths, round parity and inputs.
+
+@pytest.mark.parametrize("shape,iters,ntaps,m,mode", [
+    ((96, 130), 5, 13, 64, "vertex"),      # odd rounds: result copied back from the scratch image
+    ((121, 241), 4, 13, 255, "topcell"),   # one past a tile in both axes, the largest fused level count
+    ((7, 5), 3, 13, 20, "vertex"),         # smaller than the filter: reflection wraps several times
+    ((64, 120), 2, 1, 30, "vertex"),       # one tap: the filter is the identity, halo of one pixel
+    ((200, 333), 3, 33, 100, "topcell"),   # the widest filter, ragged tiles
+    ((1, 300), 2, 5, 17, "vertex"),        # one row
+    ((300, 1), 2, 5, 17, "topcell"),       # one column
+])
+def test_fused_rounds_bit_exact(shape, iters, ntaps, m, mode):
+    ecc = ecc_mod()
+    rng = np.random.default_rng(70 + ntaps + m)
+    img = rng.normal(size=shape).astype(np.float32)
+    r = ntaps // 2
+    if ntaps == 1:
+        taps = np.ones(1, np.float32)
+    else:
+        taps = ecc.gaussian_taps(max(1.0, r / 3.0), radius=r)
+    levels = _levels(img, m)
+    t = torch.from_numpy(img).cuda()
+    got = _run(t, taps, iters, levels, mode)
+    want, final = oracle.gaussian_pipeline(img, taps, levels.astype(np.float64), iters, mode)
+    assert np.array_equal(got, want)
+    assert np.array_equal(t.cpu().numpy(), final)
+
+
+def test_fused_pitched_rows_and_special_values():
+    """A view with pitched rows (the gaps untouched), NaN and infinities in
+    the image, levels with ties."""
+    ecc = ecc_mod()
+    rng = np.random.default_rng(81)
+    base = rng.normal(size=(150, 260)).astype(np.float32)
+    base[10, 20] = np.nan
+    base[40, 7] = np.inf
+    base[99, 200] = -np.inf
+    parent = torch.from_numpy(base.copy()).cuda()
+    view = parent[5:140, 9:250]
+    sub = np.ascontiguousarray(base[5:140, 9:250])
+    taps = ecc.gaussian_taps(1.5, radius=4)
+    levels = np.sort(np.concatenate([np.linspace(-2, 2, 40), [0.0, 0.0, 0.5]])).astype(np.float32)
+    got = _run(view, taps, 3, levels, "vertex")
+    want, final = oracle.gaussian_pipeline(sub, taps, levels.astype(np.float64), 3, "vertex")
+    assert np.array_equal(got, want)
+    after = parent.cpu().numpy()
+    assert np.array_equal(after[5:140, 9:250], final, equal_nan=True)
+    mask = np.ones(base.shape, bool)
+    mask[5:140, 9:250] = False
+    assert np.array_equal(after[mask], base[mask], equal_nan=True)
+
+
+def test_fused_paper_size_1024_square_255_levels():
+    """The paper's 1024^2 GRF with 13 taps through the fused kernel: 255
+    levels (the fused path's limit), 11 rounds (captured as a graph)."""
+    import synth
+    ecc = ecc_mod()
+    g = torch.Generator().manual_seed(64)
+    img = synth.smooth(torch.randn((1024, 1024), generator=g), 3.0).numpy().astype(np.float32)
+    taps = ecc.gaussian_taps(2.0)
+    levels = _levels(img, 255)
+    t = torch.from_numpy(img).cuda()
+    got = _run(t, taps, 11, levels, "vertex")
+    want, final = oracle.gaussian_pipeline(img, taps, levels.astype(np.float64), 11, "vertex", threads=16)
+    assert np.array_equal(got, want)
+    assert np.array_equal(t.cpu().numpy(), final)
