@@ -402,41 +402,62 @@ def run_float_levels(args):
 
 
 def run_gaussian_pipeline(args):
-    """The paper's GPU-only pipeline (Table 2): a 1024^2 float32 Gaussian
-    random field resident on the device, (ECC at 256 levels, then 13-tap
-    separable Gaussian smoothing) repeated 1, 10, 100 and 1000 times through
-    ecc_pipeline_gaussian (rounds of four or more run as one captured CUDA
-    graph launched per round).  Whole-call time from CUDA events."""
-    import numpy as np
+    """The paper's GPU-only pipeline (Table 2): a float32 Gaussian random
+    field resident on the device, (ECC at the levels, then 13-tap separable
+    Gaussian smoothing) repeated n times through ecc_pipeline_gaussian.
+    1024^2 (the paper's size) at 255 levels -- one fused kernel per round --
+    for n = 1, 10, 100, 1000, and per-round times at 1024^2 and 8192^2 (a
+    size that fills the GPU) for 255 levels (fused) and 256 levels (the
+    round as level search, stencil and one filter kernel per axis).
+    Whole-call time from CUDA events."""
     import torch
 
     import paper_2203_09087_gb300 as ecc
     import synth
-    g = torch.Generator(device="cuda")
-    g.manual_seed(5)
-    base = synth.smooth(torch.randn((1024, 1024), generator=g, device="cuda"), 3.0).contiguous()
-    levels = torch.linspace(float(base.min()), float(base.max()), 256, device="cuda").float().contiguous()
     taps = ecc.gaussian_taps(2.0)
-    plan = ecc.ecc_plan("u16", 0, 256, max_voxels=base.numel())
-    img = base.clone()
-    ecc.ecc_pipeline_gaussian(plan, img, taps, 5, levels)   # warm-up
-    ecc.ecc_status_get(plan)
-    rows = {}
-    for n in (1, 10, 100, 1000):
+
+    def field(side):
+        g = torch.Generator(device="cuda")
+        g.manual_seed(5)
+        return synth.smooth(torch.randn((side, side), generator=g, device="cuda"), 3.0).contiguous()
+
+    def rounds(base, m, n, out=None):
+        levels = torch.linspace(float(base.min()), float(base.max()), m, device="cuda").float().contiguous()
+        plan = ecc.ecc_plan("u16", 0, m, max_voxels=base.numel())
+        img = base.clone()
+        ecc.ecc_pipeline_gaussian(plan, img, taps, 4, levels)   # warm-up (captured graph)
+        ecc.ecc_status_get(plan)
         img.copy_(base)
-        out = torch.empty((n, 256), dtype=torch.int64, device="cuda")
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
         a.record()
-        ecc.ecc_pipeline_gaussian(plan, img, taps, n, levels, out=out)
+        res = ecc.ecc_pipeline_gaussian(plan, img, taps, n, levels, out=out)
         b.record()
         torch.cuda.synchronize()
         ecc.ecc_status_get(plan)
-        ms = a.elapsed_time(b)
+        assert int(res[0, -1].item()) == 1
+        return a.elapsed_time(b)
+
+    base = field(1024)
+    rows = {}
+    for n in (1, 10, 100, 1000):
+        ms = rounds(base, 255, n)
         rows[f"x{n}"] = {"overall_ms": ms, "per_iteration_ms": ms / n}
-        assert int(out[0, -1].item()) == 1
-    return {"workload": "1024^2 float32 Gaussian random field (sigma 3, seed 5), 256 levels, 13-tap Gaussian "
-                        "(sigma 2), (ECC + smoothing) x n on the device", "rounds": rows}
+    per_round = {}
+    for side, n in ((1024, 200), (8192, 20)):
+        b = base if side == 1024 else field(side)
+        for m, kind in ((255, "fused"), (256, "unfused")):
+            us = rounds(b, m, n) * 1e3 / n
+            px = side * side
+            per_round[f"{side}^2_{kind}"] = {"levels": m, "us_per_round": us, "gpx_s": px / us / 1e3,
+                                             "hbm_bytes_per_round": (8 if kind == "fused" else 24) * px,
+                                             "gb_s_at_those_bytes": (8 if kind == "fused" else 24) * px / us / 1e3}
+    return {"workload": "float32 Gaussian random field (sigma 3, seed 5), 13-tap Gaussian (sigma 2), "
+                        "(ECC + smoothing) x n on the device; 1024^2 at 255 levels for the paper's x1..x1000",
+            "rounds": rows, "per_round": per_round,
+            "bytes_note": "fused: the image read and written once per round (8 B/px, halo re-reads "
+                          "excluded); unfused: two filter passes (16 B/px), the level search (6 B/px) "
+                          "and the stencil (2 B/px)"}
 
 
 def run_config1_latency(args):
