@@ -59,16 +59,43 @@ def _peaks():
     return 6800.0, "fallback"
 
 
-def _traffic_for(kernel_digest: str):
-    """DRAM bytes per launch from the committed ncu summary, if the kernel is unchanged."""
+def _counters_for(kernel_digest: str):
+    """The 512^3 stencil launch's committed ncu counters, if the kernel is unchanged."""
     p = ROOT / "profiles" / "traffic.json"
     if not p.exists():
-        return None
+        return {}
     d = json.loads(p.read_text())
     ent = d.get("stencil_512cube_u8")
     if not ent or ent.get("kernel_digest") != kernel_digest:
-        return None
-    return ent.get("dram_bytes_per_launch")
+        return {}
+    return ent
+
+
+def _traffic_for(kernel_digest: str):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel is unchanged."""
+    return _counters_for(kernel_digest).get("dram_bytes_per_launch")
+
+
+# integer (ALU) pipe issue rate of a GB300 SM: 4 sub-partitions, each issuing
+# one ALU warp instruction every other cycle (16 lanes a sub-partition)
+ALU_WARP_INSTR_PER_SM_CYCLE = 2
+
+
+def alu_roofline(kernel_digest: str, kernel_s: float, sms: int, sm_mhz):
+    """The stencil's second roofline: ALU-pipe warp instructions per launch
+    (committed ncu count, null once the kernel changed) over the launch's
+    measured duration, against SMs x 2 per cycle x the SM clock sampled under
+    load."""
+    ent = _counters_for(kernel_digest)
+    n = ent.get("alu_warp_instr_per_launch")
+    peak = sms * ALU_WARP_INSTR_PER_SM_CYCLE * sm_mhz * 1e6 / 1e12 if sm_mhz else None
+    achieved = n / kernel_s / 1e12 if n else None
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "T warp-instr/s",
+            "frac": achieved / peak if achieved and peak else None,
+            "alu_warp_instr_per_launch": n, "warp_instr_per_launch": ent.get("warp_instr_per_launch"),
+            "peak_source": f"{sms} SMs x {ALU_WARP_INSTR_PER_SM_CYCLE} ALU warp-instr/cycle x median SM clock "
+                           f"under load ({sm_mhz} MHz)",
+            "count_source": ent.get("source") if n else "no ncu count for the current kernel sources"}
 
 
 STENCIL_SOURCES = ("ecc_bs3d.cu", "ecc_walk3.cuh", "ecc_bitlogic.cuh", "ecc_bitslice.cuh", "ecc_walk.cuh",
@@ -240,7 +267,9 @@ def run_batched(args):
     t0 = time.perf_counter()
     descs = ecc.image_descs(imgs)
     res["descriptor_build_ms"] = (time.perf_counter() - t0) * 1e3
-    for name, flags in (("batched", 0), ("per_image", ecc.ECC_FLAG_BATCH_PER_IMAGE)):
+    modes = (("batched", 0), ("per_image", ecc.ECC_FLAG_BATCH_PER_IMAGE))
+    plans = {}
+    for name, flags in modes:
         plan = ecc.ecc_plan("u8", 0, 255, max_images=len(imgs), max_voxels=total, flags=flags)
         for _ in range(3):
             ecc.ecc_compute_batch(plan, descs, out)
@@ -249,17 +278,29 @@ def run_batched(args):
         if ref is None:
             ref = got
         assert np.array_equal(ref, got)
-        reps = 5
-        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        s.record()
-        for _ in range(reps):
-            ecc.ecc_compute_batch(plan, descs, out)
-        e.record()
-        torch.cuda.synchronize()
-        ms = s.elapsed_time(e) / reps
-        res[name] = {"ms": ms, "gvox_s": total / ms / 1e6, "launches": ecc.ecc_plan_last_launches(plan)}
-    res["speedup"] = res["per_image"]["ms"] / res["batched"]["ms"]
+        plans[name] = plan
+    # trials alternate the two modes; each trial is the mean of `reps` calls,
+    # and the figures reported are the medians over the trials
+    trials, reps = 5, 5
+    ms = {name: [] for name, _ in modes}
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(trials):
+        for name, _ in modes:
+            torch.cuda.synchronize()
+            s.record()
+            for _ in range(reps):
+                ecc.ecc_compute_batch(plans[name], descs, out)
+            e.record()
+            torch.cuda.synchronize()
+            ms[name].append(s.elapsed_time(e) / reps)
+    for name, _ in modes:
+        med = statistics.median(ms[name])
+        res[name] = {"ms": med, "gvox_s": total / med / 1e6, "launches": ecc.ecc_plan_last_launches(plans[name]),
+                     "trial_ms": ms[name]}
+    ratios = [p / b for p, b in zip(ms["per_image"], ms["batched"])]
+    res["speedup"] = statistics.median(ratios)
+    res["speedup_trials"] = ratios
+    res["timing"] = f"{trials} alternating trials of {reps} calls each; medians over trials"
     return res
 
 
@@ -833,6 +874,11 @@ def main():
                     "path": "ecc_compute_host, pinned host input, chunked H2D overlapped with kernels"},
             "gpu_launches": launches_per_step * args.steps,
             "clocks": sampler.summary()}
+    if args.kernel == "default":
+        clk = line["clocks"]
+        line["roofline_alu"] = alu_roofline(_kernel_digest(), kern_avg_s,
+                                            torch.cuda.get_device_properties(local).multi_processor_count,
+                                            clk.get("sm_mhz") or clk.get("sm_max_mhz"))
     os.unlink(clock_path)
     # voxels with a nonzero signed count (the histogram insertions), from one
     # extra counting call outside the timed region

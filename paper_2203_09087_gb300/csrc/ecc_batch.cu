@@ -29,6 +29,8 @@
 
 #include "ecc_plan.h"
 #include "ecc_walk.cuh"
+#include "ecc_walk2.cuh"
+#include "ecc_walk3.cuh"
 
 namespace ecc {
 
@@ -72,7 +74,6 @@ struct BatchState {
 namespace {
 
 constexpr int kBatchWarps = 4;
-constexpr int kOut3 = 30;         // x and y extent of a 3D tile
 
 struct BatchArgs {
     const BatchHeader *hdr;
@@ -85,6 +86,7 @@ struct BatchArgs {
     int32_t smem_hist, range_check;  // range_check: the bins are guarded (range narrower than the type)
     int32_t check_all;               // every output voxel is compared with [lo, hi]
     uint32_t lo_bits, hi_bits;
+    walk3::Mul mu;
     unsigned int *status;
 };
 
@@ -96,8 +98,8 @@ __device__ __forceinline__ long long tiles_of(const BatchImage &im, int chunk2d,
         const long long ty = (im.ny + chunk2d - 1) / chunk2d;
         return (nwin * ty + 31) / 32;
     }
-    const long long tx = (im.nx + kOut3 - 1) / kOut3;
-    const long long ty = (im.ny + kOut3 - 1) / kOut3;
+    const long long tx = walk3::tiles_of((int)im.nx);
+    const long long ty = walk3::tiles_of((int)im.ny);
     const long long tz = (im.nz + chunk3d - 1) / chunk3d;
     return tx * ty * tz;
 }
@@ -166,28 +168,27 @@ __device__ void run_tile(const BatchArgs &a, const BatchImage &im, long long loc
         const int64_t first = xw * (K / 8);
         const uint32_t xex = walk::x_exist_mask(xw, im.nx);
         const uint32_t out_x = xex & 0x7ffffffeu;
-        auto fetch = [&](int64_t y, uint32_t *w) -> int {
+        auto fetch = [&](int64_t y, uint32_t *P) {
             if (y < 0 || y >= im.ny || !xex) {
 #pragma unroll
-                for (int i = 0; i <= NWORDS; ++i) w[i] = 0;
-                return 0;
+                for (int i = 0; i < K; ++i) P[i] = 0u;
+                P[K] = 0xffffffffu;
+                return;
             }
-            return walk::load_row_words<NWORDS>(im.data + y * im.pitch_y, row_bytes, first, w);
+            walk2::load_window<K>(im.data + y * im.pitch_y, row_bytes, first, P, a.mu);
+            P[K] = ~xex;
         };
-        uint32_t wn[NWORDS + 1], P[K];
-        int sh = fetch(yb - 1, wn);
-        walk::planes_from_words<K>(wn, sh, P);
-        walk::Walk2d<K, TOP> wk;
-        wk.begin(P, xex);
-        sh = fetch(yb, wn);
+        uint32_t P[K + 1];
+        fetch(yb - 1, P);
+        walk2::Walk<K, TOP> wk;
+        wk.begin(P, a.mu);
         for (int64_t y1 = yb; y1 <= ye; ++y1) {
-            uint32_t B[K];
-            walk::planes_from_words<K>(wn, sh, B);
-            if (y1 + 1 <= ye) sh = fetch(y1 + 1, wn);
+            uint32_t B[K + 1];
+            fetch(y1, B);
             if (a.check_all && y1 < ye && (~walk::in_range<K>(B, a.lo_bits, a.hi_bits) & out_x))
                 atomicOr(a.status, DEV_RANGE);
-            wk.step(B, y1 < im.ny, y1 - 1 >= 0, y1 - 1 >= yb, out_x,
-                    [&](uint32_t m, const uint32_t *X, const uint32_t *) {
+            wk.step(B, y1 - 1 >= yb, out_x, a.mu,
+                    [&](uint32_t m, const uint32_t *X) {
                         // values of row y1-1, just read (cached)
                         const unsigned char *row = im.data + (y1 - 1) * im.pitch_y + xw * (K / 8);
                         walk::emit_sparse2d(
@@ -200,59 +201,69 @@ __device__ void run_tile(const BatchArgs &a, const BatchImage &im, long long loc
                     });
         }
     } else {
-        const long long tx = (im.nx + kOut3 - 1) / kOut3;
-        const long long ty = (im.ny + kOut3 - 1) / kOut3;
-        const int64_t xt = local % tx;
-        const int64_t r = local / tx;
-        const int64_t yt = r % ty, zc = r / ty;
+        // 3D: the single-volume walker (ecc_walk3.cuh) over a tile of 32
+        // rows x 32-voxel windows (inner tiles 30 x 30 outputs, 31 along an
+        // axis at the image edge), rows read from global memory
+        const int ntx = walk3::tiles_of((int)im.nx), nty = walk3::tiles_of((int)im.ny);
+        const int xt = (int)(local % ntx);
+        const int64_t r = local / ntx;
+        const int yt = (int)(r % nty);
+        const int64_t zc = r / nty;
         const int64_t zb = zc * a.chunk3d;
         const int64_t ze = zb + a.chunk3d < im.nz ? zb + a.chunk3d : im.nz;
-        const int64_t y = yt * kOut3 - 1 + lane;
-        const int64_t xw = xt * kOut3 - 1;
-        const int64_t first = xw * (K / 8);
+        int xw, xlo, xhi, y0, ylo, yhi;
+        walk3::tile_span((int)im.nx, ntx, xt, xw, xlo, xhi);
+        walk3::tile_span((int)im.ny, nty, yt, y0, ylo, yhi);
+        const int64_t y = y0 + lane;
+        const int64_t first = (int64_t)xw * (K / 8);
         const uint32_t xex = walk::x_exist_mask(xw, im.nx);
-        const bool row_ok = y >= 0 && y < im.ny;
-        const uint32_t out_x = (lane >= 1 && lane <= kOut3 && y < im.ny) ? (xex & 0x7ffffffeu) : 0u;
-        auto fetch = [&](int64_t z, uint32_t *w) -> int {
+        const bool row_ok = y < im.ny;
+        const uint32_t xmask = (xhi == 32 ? 0xffffffffu : (1u << xhi) - 1u) & ~((1u << xlo) - 1u);
+        const uint32_t out_x = (lane >= ylo && lane < yhi && row_ok) ? (xex & xmask) : 0u;
+        const uint32_t e_row = row_ok ? ~xex : 0xffffffffu;  // existence plane of this lane's window
+        walk3::Fill fill;
+        fill.xl = xw == 0 ? 1u : 0u;
+        fill.xr = xw + 32 >= im.nx ? 0x80000000u : 0u;
+        fill.yt = lane == 0 && y0 == 0;
+        fill.yb = lane == 31 && y0 + 32 >= im.ny;
+        fill.edge = xw == 0 || xw + 32 >= im.nx || y0 == 0 || y0 + 32 >= im.ny;
+        auto fetch = [&](int64_t z, walk3::Row<K> &rw) {
             if (z < 0 || z >= im.nz || !row_ok) {
 #pragma unroll
-                for (int i = 0; i <= NWORDS; ++i) w[i] = 0;
-                return 0;
+                for (int i = 0; i < K; ++i) rw.P[i] = 0u;
+                rw.P[K] = 0xffffffffu;
+                return;
             }
-            return walk::load_row_words<NWORDS>(im.data + z * im.pitch_z + y * im.pitch_y, row_bytes, first, w);
+            walk2::load_window<K>(im.data + z * im.pitch_z + y * im.pitch_y, row_bytes, first, rw.P, a.mu);
+            rw.P[K] = e_row;
         };
-        walk::Walk3d<K, TOP> wk;
-        wk.begin();
-        const uint32_t e_row = row_ok ? ~xex : 0xffffffffu;  // existence plane of this lane's window
         // values of the plane being emitted: this lane's window in global
         // memory (just read, so cached)
         const unsigned char *vals = im.data;
-        auto emit = [&](uint32_t m, const uint32_t *Tc, const uint32_t *) {
-            walk::emit_sparse3d<TOP>(
+        auto add = [&](int v, int k) { em.add(v, k); };
+        auto add_if = [&](bool p, int v, int k) {
+            if (p) em.add(v, k);
+        };
+        auto emit = [&](uint32_t m, const uint32_t *Tc) {
+            walk3::emit3<TOP>(
                 m, Tc,
                 [&](int i) {
                     return K == 8 ? (int)__ldg(vals + i) : (int)__ldg(reinterpret_cast<const unsigned short *>(vals) + i);
                 },
-                em);
+                add, add_if);
         };
-        uint32_t wn[NWORDS + 1];
-        walk::Rows3<K> r0, r1;
-        int sh = fetch(zb - 1, wn);
-        walk::planes_from_words<K>(wn, sh, r0.P);
-        r0.P[K] = zb - 1 >= 0 ? e_row : 0xffffffffu;
-        walk::complete_rows<K>(r0);
-        sh = fetch(zb, wn);
+        walk3::Walk<K, TOP> wk;
+        wk.begin();
+        walk3::Row<K> rA, rB;
+        fetch(zb - 1, rA);
         uint32_t bad = 0;  // output voxels outside [lo, hi] (when checked)
-        for (int64_t z1 = zb;; ++z1) {
-            walk::planes_from_words<K>(wn, sh, r1.P);
-            r1.P[K] = z1 < im.nz ? e_row : 0xffffffffu;
-            if (z1 + 1 <= ze) sh = fetch(z1 + 1, wn);
-            if (a.check_all && z1 < ze) bad |= ~walk::in_range<K>(r1.P, a.lo_bits, a.hi_bits) & out_x;
-            walk::complete_rows<K>(r1);
-            vals = im.data + (z1 - 1) * im.pitch_z + (row_ok ? y : 0) * im.pitch_y + xw * (K / 8);
-            wk.step(r0, r1, z1 - 1 >= zb, out_x, emit);
-            r0 = r1;
-            if (z1 >= ze) break;
+        for (int64_t z1 = zb; z1 <= ze; ++z1) {
+            fetch(z1, rB);
+            if (a.check_all && z1 < ze) bad |= ~walk::in_range<K>(rB.P, a.lo_bits, a.hi_bits) & out_x;
+            vals = im.data + (z1 - 1) * im.pitch_z + (row_ok ? y : 0) * im.pitch_y + first;
+            wk.step(rA, rB, z1 - 1 >= zb, out_x, fill, a.mu, emit);
+#pragma unroll
+            for (int k = 0; k <= K; ++k) rA.P[k] = rB.P[k];
         }
         if (a.check_all && __any_sync(0xffffffffu, bad != 0u) && lane == 0) atomicOr(a.status, DEV_RANGE);
     }
@@ -330,6 +341,7 @@ void set_range(BatchArgs &args, const ecc_plan_s *p)
     args.check_all = args.range_check && !(p->d.flags & ECC_FLAG_NO_RANGE_CHECK);
     args.lo_bits = (uint32_t)args.lo;
     args.hi_bits = (uint32_t)(args.lo + args.nbins - 1);
+    args.mu = walk3::make_mul();
 }
 
 template <int K, bool TOP>

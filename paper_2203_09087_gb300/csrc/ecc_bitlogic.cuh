@@ -257,5 +257,27 @@ BS_HD uint32_t kappa3w(const uint32_t up[3][3], const uint32_t nW[3][3], uint32_
     return lop3<0xA8u>(lop3<0xDFu>(T[0], T[1], T[2]), T[3], out_x);
 }
 
+// The signed cell count of the pixels of row y (kappa = X0 + X1 + 2 X2 - 3,
+// bs::kappa2d's chain form: four face/square chains), from the wins in the
+// polarity the walk keeps them:
+//   wins over row y-1 at x-1, x, x+1 are ~sW[0], ~sW[1], ~sW[2];
+//   over (y, x-1): ~sE; over (y, x+1): sEr;
+//   over row y+1 at x-1, x, x+1: H0, H1, H2r.
+// Returns the mask of nonzero counts within out_x and X.
+BS_HD uint32_t kappa2w(const uint32_t sW[3], uint32_t sE, uint32_t sEr, uint32_t H0,
+                                            uint32_t H1, uint32_t H2r, uint32_t out_x, uint32_t X[3])
+{
+    // ex0 = ~sE, ex1 = sEr, ey0 = ~sW[1], ey1 = H1
+    const uint32_t b0 = lop3<0xF1u>(sE, sW[1], sW[0]);   // ~ex0 | (ey0 & w(y-1, x-1))
+    const uint32_t b1 = lop3<0x8Fu>(sEr, H1, H2r);       // ~ex1 | (ey1 & w(y+1, x+1))
+    const uint32_t b2 = lop3<0xF4u>(sW[1], sEr, sW[2]);  // ~ey0 | (ex1 & w(y-1, x+1))
+    const uint32_t b3 = lop3<0x2Fu>(H1, sE, H0);         // ~ey1 | (ex0 & w(y+1, x-1))
+    X[0] = lop3<0x96u>(b0, b1, b2);
+    X[2] = lop3<0xE8u>(b0, b1, b2);
+    X[1] = b3;
+    // sum == 3 iff X2 and exactly one of X0, X1
+    return lop3<0x9Fu>(X[2], X[0], X[1]) & out_x;
+}
+
 }  // namespace walk3
 }  // namespace ecc

@@ -31,6 +31,7 @@
 #include "ecc_scan_block.cuh"
 #include "ecc_sync.cuh"
 #include "ecc_walk.cuh"
+#include "ecc_walk2.cuh"
 
 namespace ecc {
 namespace {
@@ -65,6 +66,7 @@ struct Bs2dArgs {
     int32_t smem_hist, range_check;
     int32_t check_all;       // compare every output pixel with [lo, hi] (range narrower than the type)
     uint32_t lo_bits, hi_bits;
+    walk3::Mul mu;
     HistDst h;
     unsigned int *status;
     long long *ecc_out;      // non-null: the last CTA also scans the bins (whole image, small histogram)
@@ -95,21 +97,23 @@ __global__ void __launch_bounds__(kWarps2d * 32, 4) bs2d_kernel(const Bs2dArgs a
         const int64_t first = xw * ES;                                    // may be negative at x = 0
         const uint32_t xex = walk::x_exist_mask(xw, a.nx);
         const uint32_t out_x = xex & 0x7ffffffeu;
-        // the byte shift of the window inside its aligned words depends on the
-        // row's address (pitches need not be multiples of 4)
-        auto fetch = [&](int64_t yy, uint32_t *w) -> int {
+        // row yy as K planes and the existence plane (a row outside the
+        // image, or a window wholly outside the row, is all missing)
+        auto fetch = [&](int64_t yy, uint32_t *P) {
             if (yy < 0 || yy >= a.ny || !xex) {
 #pragma unroll
-                for (int i = 0; i <= K; ++i) w[i] = 0;
-                return 0;
+                for (int i = 0; i < K; ++i) P[i] = 0u;
+                P[K] = 0xffffffffu;
+                return;
             }
-            return walk::load_row_words<K>(a.data + yy * a.pitch, row_bytes, first, w);
+            walk2::load_window<K>(a.data + yy * a.pitch, row_bytes, first, P, a.mu);
+            P[K] = ~xex;
         };
         // values of emitted voxels come from the row just read (cached)
         const walk::Bins bins{a.smem_hist ? my_hist : nullptr, a.h.acc, a.h.lo, a.h.nbins, a.range_check,
                               a.status};
         int64_t y1 = yb;
-        auto emit = [&](uint32_t m, const uint32_t *X, const uint32_t *) {
+        auto emit = [&](uint32_t m, const uint32_t *X) {
             if (a.h.emitted && m) atomicAdd(a.h.emitted, (unsigned long long)__popc(m));  // diagnostic count
             const unsigned char *row = a.data + (y1 - 1) * a.pitch + xw * ES;
             walk::emit_sparse2d(
@@ -119,19 +123,16 @@ __global__ void __launch_bounds__(kWarps2d * 32, 4) bs2d_kernel(const Bs2dArgs a
                 },
                 bins);
         };
-        uint32_t wn[K + 1], P[K];
-        int sh = fetch(yb - 1, wn);
-        walk::planes_from_words<K>(wn, sh, P);
-        walk::Walk2d<K, TOP> wk;
-        wk.begin(P, xex);
-        sh = fetch(yb, wn);
+        uint32_t P[K + 1];
+        fetch(yb - 1, P);
+        walk2::Walk<K, TOP> wk;
+        wk.begin(P, a.mu);
         uint32_t bad = 0;  // output pixels outside [lo, hi] (when checked)
         for (; y1 <= ye; ++y1) {
-            uint32_t B[K];
-            walk::planes_from_words<K>(wn, sh, B);
-            if (y1 + 1 <= ye) sh = fetch(y1 + 1, wn);  // prefetch the next row
+            uint32_t B[K + 1];
+            fetch(y1, B);
             if (a.check_all && y1 < ye) bad |= ~walk::in_range<K>(B, a.lo_bits, a.hi_bits) & out_x;
-            wk.step(B, y1 < a.ny, y1 - 1 >= 0, y1 - 1 >= yb, out_x, emit);
+            wk.step(B, y1 - 1 >= yb, out_x, a.mu, emit);
         }
         if (a.check_all && __any_sync(0xffffffffu, bad != 0u) && lane == 0) atomicOr(a.status, DEV_RANGE);
     }
@@ -183,6 +184,7 @@ cudaError_t launch_2d_t(const Geom &g, int64_t yb, int64_t ye, const HistDst &h,
     a.check_all = range_check && a.range_check;
     a.lo_bits = (uint32_t)h.lo;
     a.hi_bits = (uint32_t)(h.lo + h.nbins - 1);
+    a.mu = walk3::make_mul();
     a.status = status;
     a.ntx = (int32_t)((g.nx + 32 * kOut - 1) / (32 * kOut));
     a.smem_hist = (size_t)HREP * h.nbins * 4 <= 160 * 1024;

@@ -25,6 +25,7 @@
 #include "ecc_plan.h"
 #include "ecc_scan_block.cuh"
 #include "ecc_walk.cuh"
+#include "ecc_walk2.cuh"
 
 namespace ecc {
 ecc_status levels_prepare(ecc_plan_s *p, const ecc_image *img, int32_t m, Geom *g);
@@ -255,24 +256,27 @@ __global__ void __launch_bounds__(kFusedThreads) fused_round2d_kernel(const Fuse
         const uint32_t out_x = xex & 0x7ffffffeu;
         const int yb = y0 + 8 * c, ye = yb + 8;                // output rows [yb, ye)
         const walk::Bins bins{hist, a.acc, 0, a.nbins, 0, a.status};
+        const walk3::Mul mu = walk3::make_mul();
+        // row gy as 8 planes and the existence plane (rows outside the
+        // image all missing)
         auto planes = [&](int gy, uint32_t *P) {
             const uint4 *q = reinterpret_cast<const uint4 *>(qbuf + ((gy - y0 + 1) * 4 + w) * 32);
             const uint4 q0 = q[0], q1 = q[1];
             const uint32_t raw[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
-            bs::transpose_u8(raw, P);
+            walk3::transpose_u8(raw, P, mu);
+            P[8] = gy >= 0 && gy < a.ny ? ~xex : 0xffffffffu;
         };
-        uint32_t P[8];
+        uint32_t P[9];
         planes(yb - 1, P);
-        walk::Walk2d<8, TOP> wk;
-        wk.begin(P, xex);
+        walk2::Walk<8, TOP> wk;
+        wk.begin(P, mu);
         for (int y1 = yb; y1 <= ye; ++y1) {
-            uint32_t B[8];
+            uint32_t B[9];
             planes(y1, B);
             const unsigned char *vrow = qbuf + ((y1 - 1 - y0 + 1) * 4 + w) * 32;
-            wk.step(B, y1 < a.ny, y1 - 1 >= 0 && y1 - 1 < a.ny, y1 - 1 >= yb && y1 - 1 < a.ny, out_x,
-                    [&](uint32_t mm, const uint32_t *X, const uint32_t *) {
-                        walk::emit_sparse2d(mm, X, [&](int i) { return (int)vrow[i]; }, bins);
-                    });
+            wk.step(B, y1 - 1 >= yb && y1 - 1 < a.ny, out_x, mu, [&](uint32_t mm, const uint32_t *X) {
+                walk::emit_sparse2d(mm, X, [&](int i) { return (int)vrow[i]; }, bins);
+            });
         }
     } else {
         // 5. the y pass, written to the other buffer (warps 1..7); with the

@@ -99,4 +99,14 @@ uint32_t h_w3_kappa3(const uint32_t *w27, uint32_t out_x, uint32_t *T)
     }
     return ecc::walk3::kappa3w(up, nW, ~w[1][1][0], w[1][1][2], sF, sD, out_x, T);
 }
+
+// The 2D walker's cell count from the 9 wins w[dy][dx] (centre unused), in
+// the walker's polarities; returns the nonzero mask, writes X.
+uint32_t h_w2_kappa2(const uint32_t *w9, uint32_t out_x, uint32_t *X)
+{
+    uint32_t w[3][3];
+    for (int i = 0; i < 9; ++i) w[i / 3][i % 3] = w9[i];
+    const uint32_t sW[3] = {~w[0][0], ~w[0][1], ~w[0][2]};
+    return ecc::walk3::kappa2w(sW, ~w[1][0], w[1][2], w[2][0], w[2][1], w[2][2], out_x, X);
+}
 }

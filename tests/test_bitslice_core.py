@@ -318,3 +318,38 @@ def test_walker_cell_count_equals_plain_on_random_and_structured_wins(h):
             nz2 = w3.h_w3_kappa3(_p(w27), out_x, _p(t2))
             assert np.array_equal(t1, t2)
             assert nz2 == (nz1 & out_x)
+
+
+def test_2d_walker_cell_count_equals_plain(h):
+    """kappa2w (the 2D walker's polarities, explicit truth tables) against
+    bs::kappa2d on random win masks of every density, and exhaustively on
+    all 2^8 patterns of one voxel."""
+    u32p = ctypes.POINTER(ctypes.c_uint32)
+    h.h_w2_kappa2.argtypes = [u32p, ctypes.c_uint32, u32p]
+    h.h_w2_kappa2.restype = ctypes.c_uint32
+    rng = np.random.default_rng(62)
+    for density in (0.1, 0.5, 0.9):
+        for _ in range(300):
+            w9 = rng.integers(0, 1 << 32, size=9, dtype=np.uint64).astype(np.uint32)
+            if density != 0.5:
+                bits = rng.uniform(size=(9, 32)) < density
+                w9 = np.array([sum(int(bits[i, x]) << x for x in range(32)) for i in range(9)], np.uint32)
+            w9[4] = 0
+            x1 = np.zeros(3, np.uint32)
+            x2 = np.zeros(3, np.uint32)
+            nz1 = h.h_kappa2d(_p(w9), _p(x1))
+            out_x = int(rng.integers(0, 1 << 32))
+            nz2 = h.h_w2_kappa2(_p(w9), out_x, _p(x2))
+            assert np.array_equal(x1, x2)
+            assert nz2 == (nz1 & out_x)
+    # every pattern of the 8 neighbours at once: bit x of input i is bit i of x's pattern
+    pats = np.arange(256, dtype=np.uint32)
+    for base in range(0, 256, 32):
+        w9 = np.zeros(9, np.uint32)
+        nbr = [0, 1, 2, 3, 5, 6, 7, 8]
+        for j, i in enumerate(nbr):
+            w9[i] = np.uint32(sum(((int(p) >> j) & 1) << x for x, p in enumerate(pats[base:base + 32])))
+        x1 = np.zeros(3, np.uint32)
+        x2 = np.zeros(3, np.uint32)
+        assert h.h_w2_kappa2(_p(w9), 0xffffffff, _p(x2)) == h.h_kappa2d(_p(w9), _p(x1))
+        assert np.array_equal(x1, x2)
