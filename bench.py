@@ -304,6 +304,42 @@ def run_batched(args):
     return res
 
 
+def time_c4_part(part: str, reps: int):
+    """The uneven batch (or only its 2D or 3D images) through one batched call:
+    one untimed call, then `reps` timed calls (CUDA events on the stream,
+    mean), then the per-image path on the same images, whose results must
+    equal the batched ones (last, so the batched launches come first)."""
+    import numpy as np
+    import torch
+
+    import paper_2203_09087_gb300 as ecc
+    import synth
+    imgs = synth.batch_images(synth.batch_specs(), device="cuda")
+    if part != "all":
+        imgs = [i for i in imgs if i.dim() == (2 if part == "2d" else 3)]
+    total = sum(int(i.numel()) for i in imgs)
+    descs = ecc.image_descs(imgs)
+    out = torch.empty((len(imgs), 256), dtype=torch.int64, device="cuda")
+    ref = torch.empty_like(out)
+    plan = ecc.ecc_plan("u8", 0, 255, max_images=len(imgs), max_voxels=total)
+    pplan = ecc.ecc_plan("u8", 0, 255, max_images=len(imgs), max_voxels=total, flags=ecc.ECC_FLAG_BATCH_PER_IMAGE)
+    ecc.ecc_compute_batch(plan, descs, out)
+    ecc.ecc_status_get(plan)
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    s.record()
+    for _ in range(reps):
+        ecc.ecc_compute_batch(plan, descs, out)
+    e.record()
+    torch.cuda.synchronize()
+    ms = s.elapsed_time(e) / reps
+    ecc.ecc_status_get(plan)
+    ecc.ecc_compute_batch(pplan, descs, ref)
+    ecc.ecc_status_get(pplan)
+    assert torch.equal(out, ref)
+    return {"workload": f"uneven batch ({part}): {len(imgs)} images", "voxels": total, "ms": ms,
+            "gvox_s": total / ms / 1e6}
+
+
 def run_single_u16(args):
     """The 16-bit single-volume workload: 1024^3 uint16 smoothed field (sigma
     8) plus 2000 bright blobs, 65536 bins (global int64 bins: the histogram
@@ -726,6 +762,9 @@ def main():
                     help="profiler runs: only the 4D case SIDE^4 uint8 (three calls after the checked one)")
     ap.add_argument("--only-c3", action="store_true",
                     help="profiler runs: only the 1024^3 uint16 volume (three calls after the checked one)")
+    ap.add_argument("--only-c4", default=None, choices=["all", "2d", "3d"],
+                    help="profiler runs: only the uneven batch, or its 2D or 3D images (three calls after "
+                         "the checked one)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     ws_env = int(os.environ.get("WORLD_SIZE", "1"))
@@ -749,6 +788,9 @@ def main():
         return
     if args.only_c3:
         print(json.dumps(time_c3(reps=3)))
+        return
+    if args.only_c4:
+        print(json.dumps(time_c4_part(args.only_c4, reps=3)))
         return
 
     import numpy as np
