@@ -48,9 +48,10 @@ struct BatchHeader {
 
 struct BatchState {
     int32_t cap = 0;
-    // device: header + descriptors, work-list prefix [cap + 1], counter
+    // device: header + descriptors, work-list prefix [cap + 1] and order [cap], counter
     unsigned char *d_desc = nullptr;
     long long *d_start = nullptr;
+    int *d_order = nullptr;
     unsigned int *d_counter = nullptr;
     // pinned staging (double-buffered) and the event of each buffer's last use
     unsigned char *h_stage[2] = {nullptr, nullptr};
@@ -78,7 +79,8 @@ constexpr int kBatchWarps = 4;
 struct BatchArgs {
     const BatchHeader *hdr;
     const BatchImage *img;
-    long long *start;  // [n + 1] exclusive prefix of tile counts
+    long long *start;  // [n + 1] exclusive prefix of tile counts, in list order
+    int *order;        // [n] image index at each list position
     unsigned int *counter;
     unsigned long long *acc;
     int32_t lo, nbins;
@@ -104,44 +106,75 @@ __device__ __forceinline__ long long tiles_of(const BatchImage &im, int chunk2d,
     return tx * ty * tz;
 }
 
-// Work list: exclusive prefix of per-image tile counts (one CTA of 1024).
+// Inclusive prefix of x over the 1024 threads of the CTA, plus *carry (the
+// sum of earlier chunks), which it then advances by this chunk's sum.
+__device__ __forceinline__ long long cta_prefix(long long x, long long *s_part, long long *carry)
+{
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const long long y = __shfl_up_sync(0xffffffffu, x, off);
+        if (lane >= off) x += y;
+    }
+    if (lane == 31) s_part[warp] = x;
+    __syncthreads();
+    if (warp == 0) {
+        long long p = s_part[lane];
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const long long y = __shfl_up_sync(0xffffffffu, p, off);
+            if (lane >= off) p += y;
+        }
+        s_part[lane] = p;
+    }
+    __syncthreads();
+    const long long incl = x + (warp ? s_part[warp - 1] : 0) + *carry;
+    __syncthreads();
+    if (tid == 1023) *carry = incl;
+    __syncthreads();
+    return incl;
+}
+
+// Work list (one CTA of 1024): the images in list order -- every 3D image
+// first, then every 2D image, each group in the caller's order -- in
+// order[], and the exclusive prefix of their tile counts in start[].  A 3D
+// tile walks a z-chunk of planes and costs about twice a 2D tile, so putting
+// the 2D tiles last leaves short tiles for the end of the run, when warps
+// run out of work at different times.
 __global__ void __launch_bounds__(1024) build_worklist(BatchArgs a)
 {
     __shared__ long long s_part[32];
     __shared__ long long s_carry;
     const int n = a.hdr->n;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int tid = threadIdx.x;
     if (tid == 0) {
         s_carry = 0;
         *a.counter = 0u;
     }
     __syncthreads();
+    // 3D images: position = number of 3D images before them (kept in start[])
     for (int base = 0; base < n; base += 1024) {
         const int i = base + tid;
-        long long c = i < n ? tiles_of(a.img[i], a.chunk2d, a.chunk3d) : 0;
-        long long x = c;
-#pragma unroll
-        for (int off = 1; off < 32; off <<= 1) {
-            const long long y = __shfl_up_sync(0xffffffffu, x, off);
-            if (lane >= off) x += y;
+        const long long f = i < n && a.img[i].ndim == 3 ? 1 : 0;
+        const long long incl = cta_prefix(f, s_part, &s_carry);
+        if (i < n) {
+            a.start[i] = incl - f;
+            if (f) a.order[incl - f] = i;
         }
-        if (lane == 31) s_part[warp] = x;
-        __syncthreads();
-        if (warp == 0) {
-            long long p = s_part[lane];
-#pragma unroll
-            for (int off = 1; off < 32; off <<= 1) {
-                const long long y = __shfl_up_sync(0xffffffffu, p, off);
-                if (lane >= off) p += y;
-            }
-            s_part[lane] = p;
-        }
-        __syncthreads();
-        const long long incl = x + (warp ? s_part[warp - 1] : 0) + s_carry;
-        if (i < n) a.start[i] = incl - c;
-        __syncthreads();
-        if (tid == 1023) s_carry = incl;
-        __syncthreads();
+    }
+    const long long n3 = s_carry;
+    __syncthreads();
+    // 2D images: after the 3D ones
+    for (int i = tid; i < n; i += 1024)
+        if (a.img[i].ndim != 3) a.order[n3 + (i - a.start[i])] = i;
+    __syncthreads();
+    if (tid == 0) s_carry = 0;
+    __syncthreads();
+    for (int base = 0; base < n; base += 1024) {
+        const int k = base + tid;
+        const long long c = k < n ? tiles_of(a.img[a.order[k]], a.chunk2d, a.chunk3d) : 0;
+        const long long incl = cta_prefix(c, s_part, &s_carry);
+        if (k < n) a.start[k] = incl - c;
     }
     if (tid == 0) a.start[n] = s_carry;
 }
@@ -150,7 +183,7 @@ template <int K, bool TOP, int ND>
 __device__ void run_tile(const BatchArgs &a, const BatchImage &im, long long local, const walk::Bins &em,
                          int lane)
 {
-    constexpr int NWORDS = K;
+    constexpr bool PF = K == 8;  // loads issued a step ahead
     const int64_t row_bytes = im.nx * (K / 8);
     if (ND == 2) {
         // Lane l walks pair q = 32 local + l: window q mod nwin of row chunk
@@ -168,36 +201,50 @@ __device__ void run_tile(const BatchArgs &a, const BatchImage &im, long long loc
         const int64_t first = xw * (K / 8);
         const uint32_t xex = walk::x_exist_mask(xw, im.nx);
         const uint32_t out_x = xex & 0x7ffffffeu;
-        auto fetch = [&](int64_t y, uint32_t *P) {
-            if (y < 0 || y >= im.ny || !xex) {
+        // 8-bit rows: a row's words are loaded one step ahead of their use
+        // (issue), so the loads are in flight while the walker works on the
+        // row before; 16-bit rows load just before use (twice the words
+        // held across a step would spill)
+        walk2::RawWin<K> raw;
+        bool raw_ok = false;
+        auto issue = [&](int64_t y) {
+            raw_ok = y >= 0 && y < im.ny && xex;
+            if (raw_ok) walk2::load_raw<K>(im.data + y * im.pitch_y, row_bytes, first, raw);
+        };
+        auto finish = [&](uint32_t *P) {
+            if (!raw_ok) {
 #pragma unroll
                 for (int i = 0; i < K; ++i) P[i] = 0u;
                 P[K] = 0xffffffffu;
                 return;
             }
-            walk2::load_window<K>(im.data + y * im.pitch_y, row_bytes, first, P, a.mu);
+            walk2::unpack<K>(raw, P, a.mu);
             P[K] = ~xex;
         };
         uint32_t P[K + 1];
-        fetch(yb - 1, P);
+        issue(yb - 1);
+        finish(P);
         walk2::Walk<K, TOP> wk;
         wk.begin(P, a.mu);
+        if (PF) issue(yb);
         for (int64_t y1 = yb; y1 <= ye; ++y1) {
             uint32_t B[K + 1];
-            fetch(y1, B);
+            if (!PF) issue(y1);
+            finish(B);
+            if (PF && y1 < ye) issue(y1 + 1);
             if (a.check_all && y1 < ye && (~walk::in_range<K>(B, a.lo_bits, a.hi_bits) & out_x))
                 atomicOr(a.status, DEV_RANGE);
             wk.step(B, y1 - 1 >= yb, out_x, a.mu,
                     [&](uint32_t m, const uint32_t *X) {
                         // values of row y1-1, just read (cached)
                         const unsigned char *row = im.data + (y1 - 1) * im.pitch_y + xw * (K / 8);
-                        walk::emit_sparse2d(
+                        walk2::emit2(
                             m, X,
                             [&](int i) {
                                 return K == 8 ? (int)__ldg(row + i)
                                               : (int)__ldg(reinterpret_cast<const unsigned short *>(row) + i);
                             },
-                            em);
+                            [&](int v, int k) { em.add(v, k); });
                     });
         }
     } else {
@@ -227,38 +274,61 @@ __device__ void run_tile(const BatchArgs &a, const BatchImage &im, long long loc
         fill.yt = lane == 0 && y0 == 0;
         fill.yb = lane == 31 && y0 + 32 >= im.ny;
         fill.edge = xw == 0 || xw + 32 >= im.nx || y0 == 0 || y0 + 32 >= im.ny;
-        auto fetch = [&](int64_t z, walk3::Row<K> &rw) {
-            if (z < 0 || z >= im.nz || !row_ok) {
+        // 8-bit rows: a plane's words are loaded one step ahead of their use
+        walk2::RawWin<K> raw;
+        bool raw_ok = false;
+        const unsigned char *row0 = im.data + (row_ok ? y : 0) * im.pitch_y;
+        auto issue = [&](int64_t z) {
+            raw_ok = z >= 0 && z < im.nz && row_ok;
+            if (raw_ok) walk2::load_raw<K>(row0 + z * im.pitch_z, row_bytes, first, raw);
+        };
+        auto finish = [&](walk3::Row<K> &rw) {
+            if (!raw_ok) {
 #pragma unroll
                 for (int i = 0; i < K; ++i) rw.P[i] = 0u;
                 rw.P[K] = 0xffffffffu;
                 return;
             }
-            walk2::load_window<K>(im.data + z * im.pitch_z + y * im.pitch_y, row_bytes, first, rw.P, a.mu);
+            walk2::unpack<K>(raw, rw.P, a.mu);
             rw.P[K] = e_row;
         };
         // values of the plane being emitted: this lane's window in global
         // memory (just read, so cached)
         const unsigned char *vals = im.data;
-        auto add = [&](int v, int k) { em.add(v, k); };
-        auto add_if = [&](bool p, int v, int k) {
-            if (p) em.add(v, k);
+        auto val_at = [&](int i) {
+            return K == 8 ? (int)__ldg(vals + i) : (int)__ldg(reinterpret_cast<const unsigned short *>(vals) + i);
         };
+        // Batch images are often rough (smoothing widths from 1 voxel), with
+        // a nonzero count at several percent of the voxels: the +-1 counts
+        // go through a loop of their own with the sign read from one plane,
+        // several per iteration (their value loads in flight together), then
+        // the rest with the full count T - 5.
         auto emit = [&](uint32_t m, const uint32_t *Tc) {
-            walk3::emit3<TOP>(
-                m, Tc,
-                [&](int i) {
-                    return K == 8 ? (int)__ldg(vals + i) : (int)__ldg(reinterpret_cast<const unsigned short *>(vals) + i);
-                },
-                add, add_if);
+            uint32_t pm, plus;
+            walk3::split_pm1_3d(Tc, pm, plus);
+            pm &= m;
+            uint32_t rest = m & ~pm;
+            // +1 where plus (negated for the top-cell complex, (-1)^3)
+            walk2::emit_units<walk2::kEmitUnroll>(pm, plus, TOP ? -1 : 1, val_at,
+                                                  [&](int v, int k) { em.add(v, k); });
+            while (rest) {
+                const int i = 31 - __clz(rest);
+                rest ^= 1u << i;
+                const int k = bs::bits_at<4>(Tc, i) - 5;
+                em.add(val_at(i), TOP ? -k : k);
+            }
         };
         walk3::Walk<K, TOP> wk;
         wk.begin();
         walk3::Row<K> rA, rB;
-        fetch(zb - 1, rA);
+        issue(zb - 1);
+        finish(rA);
+        if (PF) issue(zb);
         uint32_t bad = 0;  // output voxels outside [lo, hi] (when checked)
         for (int64_t z1 = zb; z1 <= ze; ++z1) {
-            fetch(z1, rB);
+            if (!PF) issue(z1);
+            finish(rB);
+            if (PF && z1 < ze) issue(z1 + 1);
             if (a.check_all && z1 < ze) bad |= ~walk::in_range<K>(rB.P, a.lo_bits, a.hi_bits) & out_x;
             vals = im.data + (z1 - 1) * im.pitch_z + (row_ok ? y : 0) * im.pitch_y + first;
             wk.step(rA, rB, z1 - 1 >= zb, out_x, fill, a.mu, emit);
@@ -280,12 +350,13 @@ __global__ void __launch_bounds__(kBatchWarps * 32, 4) batch_kernel(BatchArgs a)
     __syncwarp();
     const int n = a.hdr->n;
     const long long total = a.start[n];
-    int cur = -1;  // image whose bins this warp's shared histogram holds
+    int cur = -1;      // list position of the image whose bins this warp's shared histogram holds
+    int cur_img = -1;  // that image's index
     long long cur_begin = 0, cur_end = 0;  // its tile range
     auto flush = [&]() {
         if (hist && cur >= 0) {
             __syncwarp();
-            unsigned long long *dst = a.acc + (size_t)cur * a.nbins;
+            unsigned long long *dst = a.acc + (size_t)cur_img * a.nbins;
             for (int i = lane; i < a.nbins; i += 32) {
                 const int v = hist[i];
                 if (v) {
@@ -301,8 +372,8 @@ __global__ void __launch_bounds__(kBatchWarps * 32, 4) batch_kernel(BatchArgs a)
         if (lane == 0) item = (long long)atomicAdd(a.counter, 1u);
         item = __shfl_sync(0xffffffffu, item, 0);
         if (item >= total) break;
-        // image owning this tile: last i with start[i] <= item (tiles are
-        // handed out in image order, so it is usually the warp's last image)
+        // list position owning this tile: last k with start[k] <= item (tiles
+        // are handed out in list order, so it is usually the warp's last one)
         int lo = 0, hi = n - 1;
         if (cur >= 0 && item >= cur_begin && item < cur_end) {
             lo = hi = cur;
@@ -319,11 +390,12 @@ __global__ void __launch_bounds__(kBatchWarps * 32, 4) batch_kernel(BatchArgs a)
         if (lo != cur) {
             flush();
             cur = lo;
+            cur_img = a.order[lo];
             cur_begin = a.start[lo];
             cur_end = a.start[lo + 1];
         }
-        const BatchImage im = a.img[lo];
-        const walk::Bins em{hist, a.acc + (size_t)lo * a.nbins, a.lo, a.nbins, a.range_check, a.status};
+        const BatchImage im = a.img[cur_img];
+        const walk::Bins em{hist, a.acc + (size_t)cur_img * a.nbins, a.lo, a.nbins, a.range_check, a.status};
         if (im.ndim == 2)
             run_tile<K, TOP, 2>(a, im, item - a.start[lo], em, lane);
         else
@@ -377,6 +449,7 @@ cudaError_t capture_graph(ecc_plan_s *p, BatchState *b)
     args.hdr = reinterpret_cast<const BatchHeader *>(b->d_desc);
     args.img = reinterpret_cast<const BatchImage *>(b->d_desc + sizeof(BatchHeader));
     args.start = b->d_start;
+    args.order = b->d_order;
     args.counter = b->d_counter;
     args.acc = p->acc;
     args.lo = p->d.lo;
@@ -446,6 +519,7 @@ ecc_status ensure_batch(ecc_plan_s *p)
     const size_t desc_bytes = sizeof(BatchHeader) + sizeof(BatchImage) * (size_t)b->cap;
     cudaError_t e = cudaMalloc(&b->d_desc, desc_bytes);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_start, sizeof(long long) * ((size_t)b->cap + 1));
+    if (e == cudaSuccess) e = cudaMalloc(&b->d_order, sizeof(int) * (size_t)b->cap);
     if (e == cudaSuccess) e = cudaMalloc(&b->d_counter, 256);
     for (int i = 0; i < 2 && e == cudaSuccess; ++i) {
         e = cudaMallocHost(&b->h_stage[i], desc_bytes);
@@ -471,6 +545,7 @@ __global__ void init_single(BatchArgs a, BatchImage im)
     BatchHeader *hdr = const_cast<BatchHeader *>(a.hdr);
     hdr->n = 1;
     const_cast<BatchImage *>(a.img)[0] = im;
+    a.order[0] = 0;
     a.start[0] = 0;
     a.start[1] = tiles_of(im, a.chunk2d, a.chunk3d);
     *a.counter = 0u;
@@ -490,6 +565,7 @@ cudaError_t launch_batch_single(ecc_plan_s *p, const Geom &g, const HistDst &h, 
     args.hdr = reinterpret_cast<const BatchHeader *>(b->d_desc);
     args.img = reinterpret_cast<const BatchImage *>(b->d_desc + sizeof(BatchHeader));
     args.start = b->d_start;
+    args.order = b->d_order;
     args.counter = b->d_counter;
     args.acc = h.acc;
     args.lo = h.lo;
@@ -521,6 +597,7 @@ void release_batch(ecc_plan_s *p)
     }
     if (b->d_desc) cudaFree(b->d_desc);
     if (b->d_start) cudaFree(b->d_start);
+    if (b->d_order) cudaFree(b->d_order);
     if (b->d_counter) cudaFree(b->d_counter);
     delete b;
     p->batch = nullptr;

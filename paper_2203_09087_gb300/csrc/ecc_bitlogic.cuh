@@ -279,5 +279,23 @@ BS_HD uint32_t kappa2w(const uint32_t sW[3], uint32_t sE, uint32_t sEr, uint32_t
     return lop3<0x9Fu>(X[2], X[0], X[1]) & out_x;
 }
 
+// Counts of +-1, which are nearly all the nonzero counts of smooth images,
+// so the emission can take their sign from one plane.  2D (count X0 + X1 +
+// 2 X2 - 3): pm marks the +-1 (X2 ? X0 == X1 : X0 & X1), plus the +1 among
+// them (X2 & X0).
+BS_HD void split_pm1_2d(const uint32_t X[3], uint32_t &pm, uint32_t &plus)
+{
+    pm = lop3<0xC2u>(X[0], X[1], X[2]);
+    plus = X[2] & X[0];
+}
+
+// 3D (count T - 5, T = T0 + 2 T1 + 4 T2 + 8 T3): T = 4 or 6 (T2 & ~T3 & ~T0),
+// the +1 where T1.
+BS_HD void split_pm1_3d(const uint32_t T[4], uint32_t &pm, uint32_t &plus)
+{
+    pm = lop3<0x10u>(T[2], T[3], T[0]);
+    plus = T[1];
+}
+
 }  // namespace walk3
 }  // namespace ecc

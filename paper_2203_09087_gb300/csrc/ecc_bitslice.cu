@@ -116,12 +116,12 @@ __global__ void __launch_bounds__(kWarps2d * 32, 4) bs2d_kernel(const Bs2dArgs a
         auto emit = [&](uint32_t m, const uint32_t *X) {
             if (a.h.emitted && m) atomicAdd(a.h.emitted, (unsigned long long)__popc(m));  // diagnostic count
             const unsigned char *row = a.data + (y1 - 1) * a.pitch + xw * ES;
-            walk::emit_sparse2d(
+            walk2::emit2(
                 m, X,
                 [&](int i) {
                     return ES == 1 ? (int)__ldg(row + i) : (int)__ldg(reinterpret_cast<const unsigned short *>(row) + i);
                 },
-                bins);
+                [&](int v, int k) { bins.add(v, k); });
         };
         uint32_t P[K + 1];
         fetch(yb - 1, P);

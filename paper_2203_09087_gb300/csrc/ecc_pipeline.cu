@@ -275,7 +275,7 @@ __global__ void __launch_bounds__(kFusedThreads) fused_round2d_kernel(const Fuse
             planes(y1, B);
             const unsigned char *vrow = qbuf + ((y1 - 1 - y0 + 1) * 4 + w) * 32;
             wk.step(B, y1 - 1 >= yb && y1 - 1 < a.ny, out_x, mu, [&](uint32_t mm, const uint32_t *X) {
-                walk::emit_sparse2d(mm, X, [&](int i) { return (int)vrow[i]; }, bins);
+                walk2::emit2(mm, X, [&](int i) { return (int)vrow[i]; }, [&](int v, int k) { bins.add(v, k); });
             });
         }
     } else {

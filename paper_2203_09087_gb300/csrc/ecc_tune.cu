@@ -223,8 +223,13 @@ void ecc_plan_s::autotune()
             synth_fill<<<1024, 256, 0, s>>>(buf, total, es, 97, 89, d.lo, d.hi);
             for (size_t i = 0; i < imgs.size(); ++i) imgs[i].data = buf + offs[i] * es;
             float best = 1e30f;
-            for (int c2 : {16, 32, 64})
-                for (int c3 : {8, 16, 32}) {
+            // candidates: on the 4352-image uneven batch (2D sides 64-1024,
+            // 3D sides 32-256) 2D chunks of 64 rows ran 8 % slower than 16
+            // or 32, and 3D chunks of 8 or 32 planes 3-5 % slower than 16
+            // or 24 (short chunks re-read more halo planes, long ones leave
+            // warps idle at the end of the work list)
+            for (int c2 : {16, 32})
+                for (int c3 : {16, 24}) {
                     release_batch(this);
                     tuned_batch[0] = c2;
                     tuned_batch[1] = c3;

@@ -10,7 +10,7 @@
 // 1..30 are outputs, bits 0 and 31 the x halo) and walks rows; nothing in a
 // step is warp-collective, so lanes may walk different rows and images.  A
 // pixel's wins over neighbours that precede it in memory are negations of
-// their comparisons (ties to the lower linear index), as in Walk2d.
+// their comparisons (ties to the lower linear index).
 #pragma once
 
 #include <stdint.h>
@@ -26,42 +26,114 @@ using walk3::cmpk;
 using walk3::lop3;
 using walk3::Mul;
 
-// Aligned 32-bit words covering the window's bytes [first, first + 4 NW) of
-// a row of row_bytes bytes, from the aligned address at or below it, then
-// shifted into place by byte permutes and transposed into K planes.  Words
+// A window's aligned 32-bit words as loaded, before alignment: the loads can
+// be issued a step ahead of their use (load_raw), and the words shifted and
+// transposed once they are needed (unpack).
+template <int K>
+struct RawWin {
+    uint32_t w[K + 1];
+    uint32_t sel;  // byte-permute selector of the window's offset in the words
+};
+
+// Aligned 32-bit words covering the window's bytes [first, first + 4 K) of a
+// row of row_bytes bytes, from the aligned address at or below it.  Words
 // that hold no byte of the row are not read (0 instead); a window wholly
 // inside the row (the common case) loads without checks.
 template <int K>
-__device__ __forceinline__ void load_window(const unsigned char *row, int64_t row_bytes, int64_t first,
-                                            uint32_t *P, const Mul &mu)
+__device__ __forceinline__ void load_raw(const unsigned char *row, int64_t row_bytes, int64_t first, RawWin<K> &r)
 {
     constexpr int NW = K;  // 32 pixels of K bits = K words
     const uintptr_t start = reinterpret_cast<uintptr_t>(row) + (uintptr_t)first;
     const uintptr_t a0 = start & ~uintptr_t(3);
     const uintptr_t lo = reinterpret_cast<uintptr_t>(row), hi = lo + (uintptr_t)row_bytes;
-    uint32_t w[NW + 1];
     if (a0 >= lo && a0 + 4 * (NW + 1) <= hi) {
 #pragma unroll
-        for (int i = 0; i <= NW; ++i) w[i] = __ldg(reinterpret_cast<const uint32_t *>(a0) + i);
+        for (int i = 0; i <= NW; ++i) r.w[i] = __ldg(reinterpret_cast<const uint32_t *>(a0) + i);
     } else {
 #pragma unroll
         for (int i = 0; i <= NW; ++i) {
             const uintptr_t ad = a0 + 4 * i;
-            w[i] = (ad + 4 > lo && ad < hi) ? __ldg(reinterpret_cast<const uint32_t *>(ad)) : 0u;
+            r.w[i] = (ad + 4 > lo && ad < hi) ? __ldg(reinterpret_cast<const uint32_t *>(ad)) : 0u;
         }
     }
     const uint32_t sh = (uint32_t)(start & 3u);
-    const uint32_t sel = sh | ((sh + 1) << 4) | ((sh + 2) << 8) | ((sh + 3) << 12);
-    uint32_t r[NW];
+    r.sel = sh | ((sh + 1) << 4) | ((sh + 2) << 8) | ((sh + 3) << 12);
+}
+
+// The window's 32 elements, shifted into place by byte permutes and
+// transposed into K planes.
+template <int K>
+__device__ __forceinline__ void unpack(const RawWin<K> &r, uint32_t *P, const Mul &mu)
+{
+    uint32_t v[K];
 #pragma unroll
-    for (int i = 0; i < NW; ++i) r[i] = __byte_perm(w[i], w[i + 1], sel);
+    for (int i = 0; i < K; ++i) v[i] = __byte_perm(r.w[i], r.w[i + 1], r.sel);
     if (K == 8)
-        walk3::transpose_u8(r, P, mu);
+        walk3::transpose_u8(v, P, mu);
     else
-        walk3::transpose_u16(r, P, mu);
+        walk3::transpose_u16(v, P, mu);
+}
+
+template <int K>
+__device__ __forceinline__ void load_window(const unsigned char *row, int64_t row_bytes, int64_t first,
+                                            uint32_t *P, const Mul &mu)
+{
+    RawWin<K> r;
+    load_raw<K>(row, row_bytes, first, r);
+    unpack<K>(r, P, mu);
 }
 
 using walk3::kappa2w;
+
+// Adds +kp (where plus) or -kp for every element of mask pm, U elements per
+// iteration, their value loads issued together so that U are in flight at
+// once (a lane rarely has more than a few).  Bits are taken from the top
+// (one find-leading-one each).
+template <int U, class ValAt, class Add>
+__device__ __forceinline__ void emit_units(uint32_t pm, uint32_t plus, int kp, ValAt &&val_at, Add &&add)
+{
+    while (pm) {
+        int i[U], v[U];
+        uint32_t b[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            i[u] = 31 - __clz(pm | 1u);
+            b[u] = pm ? 1u << i[u] : 0u;
+            pm ^= b[u];
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            v[u] = 0;
+            if (b[u]) v[u] = val_at(i[u]);
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+            if (b[u]) add(v[u], (plus & b[u]) ? kp : -kp);
+    }
+}
+
+constexpr int kEmitUnroll = 2;
+
+// Emission of one step, per lane: m marks the window's pixels whose cell
+// count X0 + X1 + 2 X2 - 3 is nonzero (bit i: element i, value val_at(i));
+// add(v, k) adds k to the bin of value v.  The +-1 counts (in smooth images
+// nearly all) go first, their sign read from one plane; then the rest
+// (-2, -3) with the full count.
+template <class ValAt, class Add>
+__device__ __forceinline__ void emit2(uint32_t m, const uint32_t *X, ValAt &&val_at, Add &&add)
+{
+    uint32_t pm, plus;
+    walk3::split_pm1_2d(X, pm, plus);
+    pm &= m;
+    uint32_t rest = m & ~pm;
+    emit_units<kEmitUnroll>(pm, plus, 1, val_at, add);
+    while (rest) {
+        const int i = 31 - __clz(rest);
+        rest ^= 1u << i;
+        const int k = (int)((X[0] >> i) & 1u) + (int)((X[1] >> i) & 1u) + 2 * (int)((X[2] >> i) & 1u) - 3;
+        add(val_at(i), k);
+    }
+}
 
 template <int K, bool TOP>
 struct Walk {

@@ -1,10 +1,12 @@
 // ecc_walk3.cuh -- the 3D bit-sliced walker of the single-volume stencil
 // (device only).
 //
-// Same cell logic as walk::Walk3d (Sec. 2.3 "Faces introduced by a voxel",
-// Algorithm 1 regrouped per voxel; the 26 signed cell terms as 12 chain bits,
-// ecc_bitslice.cuh), arranged for the integer ALU pipe, which bounds this
-// kernel on GB300:
+// The cell logic of Sec. 2.3 "Faces introduced by a voxel" (Algorithm 1
+// regrouped per voxel; the 26 signed cell terms as 12 chain bits,
+// ecc_bitslice.cuh): each step compares plane z with plane z+1 (9 pairs per
+// voxel) and the in-plane pairs of z+1 (4), sharing the pairs with row y-1
+// through shuffles, so each neighbour pair is compared once.  Arranged for
+// the integer ALU pipe, which bounds this kernel on GB300:
 //
 //  * every one-bit shift (the x +-1 operands, the walk state) and every shift
 //    of the bit-plane transpose is a multiply by a power of two held in a

@@ -109,4 +109,8 @@ uint32_t h_w2_kappa2(const uint32_t *w9, uint32_t out_x, uint32_t *X)
     const uint32_t sW[3] = {~w[0][0], ~w[0][1], ~w[0][2]};
     return ecc::walk3::kappa2w(sW, ~w[1][0], w[1][2], w[2][0], w[2][1], w[2][2], out_x, X);
 }
+
+// The +-1 split of the emission: out[0] = pm, out[1] = plus
+void h_split_pm1_2d(const uint32_t *X, uint32_t *out) { ecc::walk3::split_pm1_2d(X, out[0], out[1]); }
+void h_split_pm1_3d(const uint32_t *T, uint32_t *out) { ecc::walk3::split_pm1_3d(T, out[0], out[1]); }
 }

@@ -20,7 +20,7 @@ def h(tmp_path_factory):
                     str(ROOT / "tests" / "bitslice_harness.cpp"), "-o", str(out)], check=True)
     lib = ctypes.CDLL(str(out))
     u32p = ctypes.POINTER(ctypes.c_uint32)
-    for n in ("h_transpose_u8", "h_transpose_u16", "h_count12"):
+    for n in ("h_transpose_u8", "h_transpose_u16", "h_count12", "h_split_pm1_2d", "h_split_pm1_3d"):
         getattr(lib, n).argtypes = [u32p, u32p]
     for n in ("h_ge8", "h_ge16"):
         getattr(lib, n).argtypes = [u32p, u32p]
@@ -353,3 +353,22 @@ def test_2d_walker_cell_count_equals_plain(h):
         x2 = np.zeros(3, np.uint32)
         assert h.h_w2_kappa2(_p(w9), 0xffffffff, _p(x2)) == h.h_kappa2d(_p(w9), _p(x1))
         assert np.array_equal(x1, x2)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+def test_emission_split_of_unit_counts(h, dim):
+    """The emission's split of the counts: pm marks exactly the voxels whose
+    count is +1 or -1 and plus exactly the +1 among them, for every value
+    of the count planes (bit x of the planes holds pattern x)."""
+    nplanes = 3 if dim == 2 else 4
+    pats = np.arange(1 << nplanes)
+    planes = np.array([sum(((int(p) >> k) & 1) << x for x, p in enumerate(pats)) for k in range(nplanes)],
+                      np.uint32)
+    out = np.zeros(2, np.uint32)
+    getattr(h, f"h_split_pm1_{dim}d")(_p(planes), _p(out))
+    for x, p in enumerate(pats):
+        bits = [(int(p) >> k) & 1 for k in range(nplanes)]
+        count = bits[0] + bits[1] + 2 * bits[2] - 3 if dim == 2 else int(p) - 5
+        assert ((int(out[0]) >> x) & 1) == (count in (1, -1)), (dim, p)
+        if count in (1, -1):
+            assert ((int(out[1]) >> x) & 1) == (count == 1), (dim, p)
