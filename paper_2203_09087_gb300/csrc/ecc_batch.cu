@@ -309,7 +309,7 @@ __device__ void run_tile(const BatchArgs &a, const BatchImage &im, long long loc
             pm &= m;
             uint32_t rest = m & ~pm;
             // +1 where plus (negated for the top-cell complex, (-1)^3)
-            walk2::emit_units<walk2::kEmitUnroll>(pm, plus, TOP ? -1 : 1, val_at,
+            walk2::emit_units<walk2::kEmitUnroll3d>(pm, plus, TOP ? -1 : 1, val_at,
                                                   [&](int v, int k) { em.add(v, k); });
             while (rest) {
                 const int i = 31 - __clz(rest);

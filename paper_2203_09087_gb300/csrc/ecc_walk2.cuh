@@ -95,24 +95,32 @@ __device__ __forceinline__ void emit_units(uint32_t pm, uint32_t plus, int kp, V
     while (pm) {
         int i[U], v[U];
         uint32_t b[U];
+        i[0] = 31 - __clz(pm);  // the loop's own element: always present
+        b[0] = 1u << i[0];
+        pm ^= b[0];
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
+        for (int u = 1; u < U; ++u) {
             i[u] = 31 - __clz(pm | 1u);
             b[u] = pm ? 1u << i[u] : 0u;
             pm ^= b[u];
         }
+        v[0] = val_at(i[0]);
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
+        for (int u = 1; u < U; ++u) {
             v[u] = 0;
             if (b[u]) v[u] = val_at(i[u]);
         }
+        add(v[0], (plus & b[0]) ? kp : -kp);
 #pragma unroll
-        for (int u = 0; u < U; ++u)
+        for (int u = 1; u < U; ++u)
             if (b[u]) add(v[u], (plus & b[u]) ? kp : -kp);
     }
 }
 
-constexpr int kEmitUnroll = 2;
+// Elements per iteration: measured on the uneven batch, 2 for the 2D
+// walker's windows and 3 for the 3D tiles (3 or 4 gave the 2D part nothing,
+// the 3D part 8 % more than 2).
+constexpr int kEmitUnroll2d = 2, kEmitUnroll3d = 3;
 
 // Emission of one step, per lane: m marks the window's pixels whose cell
 // count X0 + X1 + 2 X2 - 3 is nonzero (bit i: element i, value val_at(i));
@@ -126,7 +134,7 @@ __device__ __forceinline__ void emit2(uint32_t m, const uint32_t *X, ValAt &&val
     walk3::split_pm1_2d(X, pm, plus);
     pm &= m;
     uint32_t rest = m & ~pm;
-    emit_units<kEmitUnroll>(pm, plus, 1, val_at, add);
+    emit_units<kEmitUnroll2d>(pm, plus, 1, val_at, add);
     while (rest) {
         const int i = 31 - __clz(rest);
         rest ^= 1u << i;
