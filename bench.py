@@ -304,6 +304,30 @@ def run_batched(args):
     return res
 
 
+def time_c1(reps: int):
+    """The 256^2 uint8 image: one checked call, then `reps` calls each queued
+    behind a spin kernel and timed with CUDA events (the device work alone)."""
+    import numpy as np
+    import torch
+
+    import paper_2203_09087_gb300 as ecc
+    import synth
+    t = torch.from_numpy(synth.config1_uniform_2d()).cuda()
+    plan = ecc.ecc_plan("u8", 0, 255, max_voxels=t.numel())
+    out = ecc.ecc_compute(plan, t)
+    ecc.ecc_status_get(plan)
+    ts = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda._sleep(200_000)
+        a.record()
+        ecc.ecc_compute(plan, t, out)
+        b.record()
+        b.synchronize()
+        ts.append(a.elapsed_time(b) * 1e3)
+    return {"workload": "256x256 uint8 uniform [0,255], seed 0, 256 bins", "device_us_p50": float(np.median(ts))}
+
+
 def time_c4_part(part: str, reps: int):
     """The uneven batch (or only its 2D or 3D images) through one batched call:
     one untimed call, then `reps` timed calls (CUDA events on the stream,
@@ -540,8 +564,10 @@ def run_gaussian_pipeline(args):
 def run_config1_latency(args):
     """C1, the 256x256 uint8 uniform image: too small to fill the GPU, so the
     figure is the latency of one ecc_compute call (stencil and scan) measured
-    with CUDA events on the stream, median of 200 calls, and the same for a
-    call through ecc_compute_host (host image in, host ECC out)."""
+    with CUDA events on the stream, median of 200 calls -- on an idle stream
+    (launch latency included) and queued behind a spin kernel (the device
+    work alone) -- and the same for a call through ecc_compute_host (host
+    image in, host ECC out, host clock)."""
     import numpy as np
     import torch
 
@@ -560,6 +586,18 @@ def run_config1_latency(args):
         b.record()
         b.synchronize()
         ts.append(a.elapsed_time(b) * 1e3)
+    # the same with the stream kept busy ahead of the call (a spin kernel),
+    # so the events bracket the device work alone and not the host's launch
+    # latency on an idle stream
+    ks = []
+    for _ in range(200):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda._sleep(200_000)
+        a.record()
+        ecc.ecc_compute(plan, t, out)
+        b.record()
+        b.synchronize()
+        ks.append(a.elapsed_time(b) * 1e3)
     host = np.ascontiguousarray(img)
     hout = np.empty(256, np.int64)
     hs = []
@@ -569,7 +607,11 @@ def run_config1_latency(args):
         hs.append((time.perf_counter() - t0) * 1e6)
     assert np.array_equal(hout, out.cpu().numpy())
     return {"workload": "256x256 uint8 uniform [0,255], seed 0, 256 bins", "device_call_us_p50": float(np.median(ts)),
-            "device_call_us_p99": float(np.percentile(ts, 99)), "host_call_us_p50": float(np.median(hs))}
+            "device_call_us_p99": float(np.percentile(ts, 99)),
+            "device_call_timing": "events on an idle stream around one call: includes the launch latency",
+            "device_busy_stream_us_p50": float(np.median(ks)), "device_busy_stream_us_p99": float(np.percentile(ks, 99)),
+            "device_busy_stream_timing": "events around one call queued behind a spin kernel: the device work alone",
+            "host_call_us_p50": float(np.median(hs))}
 
 
 def run_cpu_baselines(args):
@@ -762,6 +804,8 @@ def main():
                     help="profiler runs: only the 4D case SIDE^4 uint8 (three calls after the checked one)")
     ap.add_argument("--only-c3", action="store_true",
                     help="profiler runs: only the 1024^3 uint16 volume (three calls after the checked one)")
+    ap.add_argument("--only-c1", action="store_true",
+                    help="profiler runs: only the 256^2 uint8 image (ten calls after the checked one)")
     ap.add_argument("--only-c4", default=None, choices=["all", "2d", "3d"],
                     help="profiler runs: only the uneven batch, or its 2D or 3D images (three calls after "
                          "the checked one)")
@@ -788,6 +832,9 @@ def main():
         return
     if args.only_c3:
         print(json.dumps(time_c3(reps=3)))
+        return
+    if args.only_c1:
+        print(json.dumps(time_c1(reps=10)))
         return
     if args.only_c4:
         print(json.dumps(time_c4_part(args.only_c4, reps=3)))

@@ -48,21 +48,23 @@ struct Cfg {
 
 // ----------------------------------------------------------------- 2D kernel
 //
-// Lanes along x: lane l of a warp holds the window [x0-1, x0+31) with
-// x0 = X0 + 30 l, so a warp covers 960 columns; the warp walks rows.  Rows
-// come straight from global memory as aligned 32-bit words (coalesced across
-// the warp; any pitch and alignment; words that hold no byte of the row are
-// not read), with the next row prefetched while the current one is
-// processed.  Each voxel pair is compared once: the row pair (y, y+1) in
-// three x offsets and the in-row pair, the earlier voxel's wins being the
-// negations.  Warps are independent work-list walkers; the CTA only shares
-// the privatized histogram.
+// A lane holds a window [30 t - 1, 30 t + 31) of a row and walks a chunk
+// of rows; the lanes of a warp take consecutive (window, row chunk) pairs,
+// windows fastest, so in a wide image they sit side by side in one row (a
+// warp covers 960 columns) and in a narrow one they go on into the next
+// chunks instead of idling (a 256-wide image keeps all 32 lanes busy, not
+// 9).  Rows come straight from global memory as aligned 32-bit words
+// (coalesced across the lanes of a row; any pitch and alignment; words that
+// hold no byte of the row are not read).  Each voxel pair is compared once:
+// the row pair (y, y+1) in three x offsets and the in-row pair, the earlier
+// voxel's wins being the negations.  Warps are independent work-list
+// walkers; the CTA only shares the privatized histogram.
 
 struct Bs2dArgs {
     const unsigned char *data;
     int64_t nx, ny, pitch;
     int64_t y_begin, y_end;
-    int32_t ntx, nyc, ychunk, nitems;
+    int32_t nwin, nyc, ychunk, nitems;  // 30-column windows per row, row chunks, rows per chunk, warp items
     int32_t smem_hist, range_check;
     int32_t check_all;       // compare every output pixel with [lo, hi] (range narrower than the type)
     uint32_t lo_bits, hi_bits;
@@ -90,12 +92,18 @@ __global__ void __launch_bounds__(kWarps2d * 32, 4) bs2d_kernel(const Bs2dArgs a
     const int64_t row_bytes = a.nx * ES;
 
     for (int item = blockIdx.x * kWarps2d + warp; item < a.nitems; item += gridDim.x * kWarps2d) {
-        const int xt = item % a.ntx, yc = item / a.ntx;
-        const int64_t yb = a.y_begin + (int64_t)yc * a.ychunk;
-        const int64_t ye = yb + a.ychunk < a.y_end ? yb + a.ychunk : a.y_end;
-        const int64_t xw = (int64_t)xt * (32 * kOut) + kOut * lane - 1;  // voxel of window bit 0
-        const int64_t first = xw * ES;                                    // may be negative at x = 0
-        const uint32_t xex = walk::x_exist_mask(xw, a.nx);
+        // lane l takes (window, row chunk) pair q = 32 item + l, windows
+        // fastest: in a wide image the warp's 32 windows sit side by side
+        // in one row chunk; in a narrow one (or where a row's windows run
+        // out) the lanes go on into the next chunks, so every lane has work
+        const int64_t q = 32 * (int64_t)item + lane;
+        const bool active = q < (int64_t)a.nwin * a.nyc;
+        const int64_t yc = q / a.nwin, xt = q - yc * a.nwin;
+        const int64_t yb = a.y_begin + yc * a.ychunk;
+        const int64_t ye = !active ? yb - 1 : (yb + a.ychunk < a.y_end ? yb + a.ychunk : a.y_end);
+        const int64_t xw = kOut * xt - 1;  // voxel of window bit 0
+        const int64_t first = xw * ES;     // may be negative at x = 0
+        const uint32_t xex = active ? walk::x_exist_mask(xw, a.nx) : 0u;
         const uint32_t out_x = xex & 0x7ffffffeu;
         // row yy as K planes and the existence plane (a row outside the
         // image, or a window wholly outside the row, is all missing)
@@ -186,7 +194,8 @@ cudaError_t launch_2d_t(const Geom &g, int64_t yb, int64_t ye, const HistDst &h,
     a.hi_bits = (uint32_t)(h.lo + h.nbins - 1);
     a.mu = walk3::make_mul();
     a.status = status;
-    a.ntx = (int32_t)((g.nx + 32 * kOut - 1) / (32 * kOut));
+    if ((g.nx + kOut - 1) / kOut > 2147483647) return cudaErrorNotSupported;
+    a.nwin = (int32_t)((g.nx + kOut - 1) / kOut);
     a.smem_hist = (size_t)HREP * h.nbins * 4 <= 160 * 1024;
     const size_t smem = a.smem_hist ? (size_t)HREP * h.nbins * 4 : 0;
     auto kern = bs2d_kernel<T, TOP, HREP>;
@@ -209,17 +218,18 @@ cudaError_t launch_2d_t(const Geom &g, int64_t yb, int64_t ye, const HistDst &h,
     if (per_sm_cached < 1) return cudaErrorNotSupported;
     const int64_t warps_max = (int64_t)num_sms * per_sm_cached * kWarps2d;
     const int64_t depth = ye - yb;
-    int64_t nyc = (3 * warps_max + a.ntx - 1) / a.ntx;
-    // chunks of at least 16 rows (each re-reads one halo row), unless that
-    // leaves fewer than four warps per SM: small images walk 4-row chunks
-    // (a warp's walk is a chain of dependent row steps)
-    const int64_t cap16 = (depth + 15) / 16, cap4 = (depth + 3) / 4;
-    const int64_t cap = cap16 * a.ntx >= 4 * (int64_t)num_sms ? cap16 : cap4;
+    // about three warp items per resident warp, in chunks of at least 16
+    // rows (each re-reads one halo row) unless that leaves fewer than four
+    // warps per SM: small images walk single rows (a lane's walk is a chain
+    // of dependent row steps)
+    int64_t nyc = (3 * warps_max * 32 + a.nwin - 1) / a.nwin;
+    const int64_t cap16 = (depth + 15) / 16;
+    const int64_t cap = cap16 * a.nwin >= 4 * (int64_t)num_sms * 32 ? cap16 : depth;
     if (nyc > cap) nyc = cap;
     if (nyc < 1) nyc = 1;
     a.ychunk = (int32_t)((depth + nyc - 1) / nyc);
     a.nyc = (int32_t)((depth + a.ychunk - 1) / a.ychunk);
-    const int64_t items = (int64_t)a.ntx * a.nyc;
+    const int64_t items = ((int64_t)a.nwin * a.nyc + 31) / 32;
     if (items > 2147483647) return cudaErrorNotSupported;
     a.nitems = (int32_t)items;
     int64_t ctas = (items + kWarps2d - 1) / kWarps2d;

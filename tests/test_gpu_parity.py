@@ -47,7 +47,9 @@ def _run(img_t, lo, hi, mode, kernel="default", with_vcec=False):
     return res
 
 
-SHAPES_2D = [(1, 1), (1, 37), (37, 1), (2, 2), (31, 33), (100, 77), (256, 256), (129, 1030), (700, 45)]
+SHAPES_2D = [(1, 1), (1, 37), (37, 1), (2, 2), (31, 33), (100, 77), (256, 256), (129, 1030), (700, 45),
+             # either side of the 2D kernel's narrow mapping (one 30-column window per lane below 960)
+             (64, 30), (2, 61), (3, 959), (5, 960), (33, 991)]
 SHAPES_3D = [(1, 1, 1), (1, 5, 7), (4, 1, 9), (3, 33, 65), (17, 40, 129), (40, 64, 64), (9, 97, 31), (2, 130, 300)]
 
 
