@@ -294,7 +294,13 @@ void scheduler_main(ecc_server_s *s)
             launch_batch(s, lk, slot);
             launched = true;
         }
-        if (launched) continue;
+        if (launched) {
+            // the completion thread may be asleep with no slot busy: wake it
+            // so the new launch's completion is seen when it happens, not at
+            // the end of its idle wait
+            s->cv_sched.notify_all();
+            continue;
+        }
         if (s->stopping && s->pending.empty() && s->admitted.empty()) {
             bool any_busy = false;
             for (auto &slot : s->slots) any_busy = any_busy || slot.busy;
