@@ -177,7 +177,8 @@ def level_bins_rows(img: np.ndarray, levels, begin: int, end: int, mode: str = V
 
 def ecc_levels(img: np.ndarray, levels, mode: str = VERTEX, threads: int = 1) -> np.ndarray:
     """ECC of a float32 image at ascending thresholds: int64[m], entry i =
-    chi(K_{<= levels[i]}).  NaN voxels count as +infinity."""
+    chi(K_{<= levels[i]}).  A NaN voxel is in no sublevel set: it lies above
+    every level, +infinity included."""
     lib = load()
     img = np.ascontiguousarray(img, dtype=np.float32)
     end = row_extent(img.shape, mode)
@@ -200,6 +201,26 @@ def ecc_levels(img: np.ndarray, levels, mode: str = VERTEX, threads: int = 1) ->
     if errors:
         raise errors[0]
     return ecc_from_vcec(np.sum(parts, axis=0).astype(np.int64), lib)
+
+
+def present_levels(img: np.ndarray) -> np.ndarray:
+    """Eq. 1's thresholds of a float32 image: the values present in it,
+    distinct and ascending (t_1 < t_2 < ... < t_n, Sec. 2.2).  NaN voxels
+    define no threshold (they count as +infinity, above every level), and
+    -0.0 is the value 0.0 (it compares equal to it, so it is the same
+    threshold), returned as +0.0.  A library sort-unique is the step."""
+    v = np.asarray(img, dtype=np.float32).ravel()
+    v = v[~np.isnan(v)]
+    return np.unique(v + np.float32(0.0)).astype(np.float32)
+
+
+def ecc_present(img: np.ndarray, mode: str = VERTEX, threads: int = 1):
+    """The paper's ECC sequence of a float32 image (Eq. 1): (levels, ecc)
+    with levels = present_levels(img) and ecc[i] = chi(K_{<= levels[i]})."""
+    lv = present_levels(img)
+    if lv.size == 0:  # every voxel NaN: no threshold
+        return lv, np.zeros(0, np.int64)
+    return lv, ecc_levels(img, lv, mode, threads)
 
 
 def row_extent(img_shape, mode: str = VERTEX) -> int:

@@ -221,12 +221,14 @@ void oracle_ecc_from_vcec(const int64_t *vcec, int64_t nbins, int64_t *ecc)
  * its vertices, or min of its top cofaces), and (-1)^dim added to bin i =
  * the first index whose level is >= the value; a cell above t_{m-1} lies in
  * no sublevel set and is skipped.  The prefix sum of the m bins is then the
- * ECC at the m thresholds.  A NaN voxel counts as +infinity.
+ * ECC at the m thresholds.  A NaN voxel is in no sublevel set (v <= t is
+ * false for it at every t): it lies above every level, +infinity included,
+ * so a cell with a NaN vertex (vertex complex) or with only NaN cofaces
+ * (top-cell complex) is counted at no level.
  */
 static double float_value(const float *img, int64_t lin)
 {
-    const double v = (double)img[lin];
-    return v != v ? (double)INFINITY : v;
+    return (double)img[lin];
 }
 
 /* First index i in [0, m] with levels[i] >= v (m if none). */
@@ -267,13 +269,16 @@ int oracle_levels_vertex_rows(const float *img, int ndim, const int64_t *dims, i
             }
             if (!exists) continue;
             double value = -(double)INFINITY;
+            int nan_vertex = 0;
             for (unsigned B = 0; B < n_subsets; ++B) {
                 if (B & ~A) continue;
                 int64_t q[ORACLE_MAX_DIM];
                 for (int a = 0; a < ndim; ++a) q[a] = p[a] + ((B >> a) & 1u);
                 const double v = float_value(img, linear_index(ndim, dims, q));
-                if (v > value) value = v;
+                if (v != v) nan_vertex = 1;
+                else if (v > value) value = v;
             }
+            if (nan_vertex) continue;
             const int64_t i = first_level_at_or_above(levels, m, value);
             if (i < m) bins[i] += (dim % 2 == 0) ? 1 : -1;
         }
@@ -310,12 +315,17 @@ int oracle_levels_topcell_rows(const float *img, int ndim, const int64_t *dims, 
             }
         }
         double value = (double)INFINITY;
+        int any_coface = 0;  /* a coface that is not NaN */
         int64_t v_hi[ORACLE_MAX_DIM], q[ORACLE_MAX_DIM];
         for (int a = 0; a < ndim; ++a) { q[a] = first[a]; v_hi[a] = last[a] + 1; }
         do {
             const double v = float_value(img, linear_index(ndim, dims, q));
-            if (v < value) value = v;
+            if (v == v) {
+                any_coface = 1;
+                if (v < value) value = v;
+            }
         } while (next_coord(ndim, first, v_hi, q));
+        if (!any_coface) continue;
         const int64_t i = first_level_at_or_above(levels, m, value);
         if (i < m) bins[i] += (dim % 2 == 0) ? 1 : -1;
     } while (next_coord(ndim, lo_a, hi_a, e));

@@ -23,7 +23,7 @@ def _rand_img(rng, shape):
 
 def _rand_levels(rng, m):
     """Ascending levels, with repeats and values outside the image range."""
-    cand = np.array([-2.0, -1.5, -0.3, 0.0, 0.4, 0.5, 0.5000001, 1.0, 2.0, 3.75, 5.0], np.float64)
+    cand = np.array([-2.0, -1.5, -0.3, 0.0, 0.4, 0.5, 0.5000001, 1.0, 2.0, 3.75, 5.0, np.inf], np.float64)
     return np.sort(rng.choice(cand, size=m, replace=True))
 
 
@@ -97,19 +97,30 @@ LEVEL_MUTANTS = [
     ("float min replaced by first coface", "if (v < value) value = v;", "if (value == (double)INFINITY) value = v;", 1),
     ("sign dropped in float top cells", "if (i < m) bins[i] += (dim % 2 == 0) ? 1 : -1;",
      "if (i < m) bins[i] += 1;", 1),
-    ("NaN taken as -infinity", "return v != v ? (double)INFINITY : v;", "return v != v ? -(double)INFINITY : v;", 0),
+    ("NaN vertex ignored", "if (v != v) nan_vertex = 1;", "if (v != v) nan_vertex = 0;", 0),
+    ("NaN cofaces counted at +infinity", "if (!any_coface) continue;", "", 0),
 ]
 
 
 def _level_pins_pass(lib) -> bool:
     rng = np.random.default_rng(35)
+    # fixed cases first: NaN inside (a hole at every level, +infinity
+    # included), at a corner and in a row, with +infinity a level
+    fixed = [(np.array([[1.0, 0.0, 2.0], [0.5, np.nan, 1.0], [3.0, 0.0, -1.0]], np.float32),
+              np.array([0.0, 2.0, np.inf])),
+             (np.array([[np.nan, 1.0, 2.0], [0.5, np.inf, np.nan]], np.float32), np.array([0.0, 2.0, np.inf])),
+             (np.array([[[np.nan, np.nan], [3.0, -1.0]]], np.float32), np.array([-1.0, np.inf]))]
     for mode in MODES:
         fn = lib.oracle_levels_vertex_rows if mode == "vertex" else lib.oracle_levels_topcell_rows
-        for _ in range(60):
-            nd = int(rng.integers(2, 4))
-            shape = tuple(int(x) for x in rng.integers(1, 5, size=nd))
-            img = np.ascontiguousarray(_rand_img(rng, shape))
-            levels = _rand_levels(rng, int(rng.integers(1, 6)))
+        for k in range(60 + len(fixed)):
+            if k < len(fixed):
+                img, levels = fixed[k]
+                shape = img.shape
+            else:
+                nd = int(rng.integers(2, 4))
+                shape = tuple(int(x) for x in rng.integers(1, 5, size=nd))
+                img = np.ascontiguousarray(_rand_img(rng, shape))
+                levels = _rand_levels(rng, int(rng.integers(1, 6)))
             dims = np.asarray(shape, np.int64)
             bins = np.zeros(levels.size, np.int64)
             import ctypes
