@@ -499,7 +499,50 @@ def run_float_levels(args):
             "gvox_s": nvox / (ms * 1e-3) / 1e9, "ms_per_step": ms,
             "stencil_us": kern_ms / max(kern_n, 1) * 1e3,
             "hbm": {"bytes_per_step": alg, "achieved_gbs": alg / (ms * 1e-3) / 1e9, "peak": peak,
-                    "frac": alg / (ms * 1e-3) / 1e9 / peak, "peak_source": src}}
+                    "frac": alg / (ms * 1e-3) / 1e9 / peak, "peak_source": src},
+            "present_levels": run_present_levels(f, levels, flush)}
+
+
+def run_present_levels(f, levels, flush):
+    """The paper's own thresholds (Eq. 1: the values present): the same field
+    rounded to its 1024 quantile levels, so it holds 1024 distinct float32
+    values as the paper's Gaussian random fields do (those levels that some
+    voxel takes).  Times ecc_levels_present (three launches) and
+    ecc_compute_present (levels, one host read of their number, then the ECC
+    at them), CUDA events, L2 flushed before each call; the levels found must
+    be the field's distinct values (torch.unique as the check)."""
+    import torch
+
+    import paper_2203_09087_gb300 as ecc
+    idx = torch.bucketize(f, levels).clamp_(max=levels.numel() - 1)
+    fq = levels[idx].contiguous()
+    del idx
+    nvox = fq.numel()
+    plan = ecc.ecc_plan("u16", 0, 65535, max_voxels=nvox)
+    lv, cnt = ecc.ecc_levels_present(plan, fq, max_levels=4096)
+    n = int(cnt.item())
+    want = torch.unique(fq)
+    assert n == int(want.numel()) and torch.equal(lv[:n], want)
+    times = {"levels_present": [], "compute_present": []}
+    for i in range(8):
+        for name in times:
+            flush.fill_(i & 0xFF)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            if name == "levels_present":
+                ecc.ecc_levels_present(plan, fq, max_levels=4096, levels_out=lv, count_out=cnt)
+            else:
+                ecc.ecc_compute_present(plan, fq, max_levels=4096)
+            b.record()
+            torch.cuda.synchronize()
+            times[name].append(a.elapsed_time(b))
+    ecc.ecc_status_get(plan)
+    med = {k: sorted(v)[len(v) // 2] for k, v in times.items()}
+    return {"workload": "the 512^3 field rounded to its 1024 quantile levels (1024 distinct float32 values)",
+            "distinct_values": n, "levels_present_ms": med["levels_present"],
+            "compute_present_ms": med["compute_present"],
+            "levels_present_gvox_s": nvox / (med["levels_present"] * 1e-3) / 1e9,
+            "compute_present_gvox_s": nvox / (med["compute_present"] * 1e-3) / 1e9}
 
 
 def run_gaussian_pipeline(args):

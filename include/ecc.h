@@ -182,6 +182,39 @@ ecc_status ecc_compute_host(ecc_plan_t plan, const ecc_image *h_img, int64_t *h_
 ecc_status ecc_compute_levels(ecc_plan_t plan, const ecc_image *img, const float *d_levels, int32_t m,
                               int64_t *d_ecc, void *stream);
 
+/* Eq. 1's thresholds of a float32 image, found on the device: the values
+ * present in it, distinct and ascending, t_1 < ... < t_n (Sec. 2.2: the
+ * paper's ECC is indexed by them).  ecc_compute_levels at these n levels is
+ * then the paper's ECC sequence.  A NaN voxel is in no sublevel set and
+ * defines no threshold; -0.0 is the value 0.0 and is reported as +0.0.
+ *   plan        any plan; its max_voxels bounds the image.  A hash table of
+ *               about 8 * max_levels bytes is allocated in it on first use.
+ *   img         device image, dtype ECC_F32, 4-byte aligned pitches.
+ *   d_levels    device float[max_levels], written with the n levels in
+ *               ascending order when n <= max_levels (untouched otherwise).
+ *   max_levels  1..65536.
+ *   d_count     device int32, written n, or max_levels + 1 when the image
+ *               holds more distinct values than that.
+ * Asynchronous on `stream` (three launches; the caller reads d_count to
+ * learn n).  Errors returned directly: ECC_E_INVALID, ECC_E_BUSY (more
+ * voxels than max_voxels), ECC_E_NOMEM, ECC_E_CUDA. */
+ecc_status ecc_levels_present(ecc_plan_t plan, const ecc_image *img, float *d_levels, int32_t max_levels,
+                              int32_t *d_count, void *stream);
+
+/* The paper's ECC sequence of a float32 image (Eq. 1 at its present values):
+ * ecc_levels_present, then ecc_compute_levels at the n levels found.
+ *   plan        as for ecc_compute_levels, with hi >= the number of
+ *               distinct values (an ECC_U16 plan with hi = 65535 takes any).
+ *   d_levels    device float[max_levels]: the levels (first n entries).
+ *   h_count     host int32, written n (max_levels + 1 when there are more).
+ *   d_ecc       device int64[max_levels]: d_ecc[i] = chi(K_{<= d_levels[i]})
+ *               for i < n.
+ * Synchronizes `stream` once, to read n.  Errors as ecc_levels_present and
+ * ecc_compute_levels, plus ECC_E_BUSY (nothing computed) when n >
+ * max_levels or when the plan does not cover n levels (lo = 0, hi >= n). */
+ecc_status ecc_compute_present(ecc_plan_t plan, const ecc_image *img, float *d_levels, int32_t max_levels,
+                               int32_t *h_count, int64_t *d_ecc, void *stream);
+
 /* The paper's GPU-only pipeline (Sec. 4 "GPU-only pipeline", Table 2): a
  * float32 image resident on the device goes through `iterations` rounds of
  * (1) its ECC at the m thresholds d_levels (exactly ecc_compute_levels) and

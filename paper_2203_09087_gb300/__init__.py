@@ -48,6 +48,8 @@ from ._binding import (  # noqa: F401
     ecc_compute_batch,
     ecc_compute_host,
     ecc_compute_levels,
+    ecc_compute_present,
+    ecc_levels_present,
     ecc_compute_nd,
     ecc_pipeline_gaussian,
     gaussian_taps,

@@ -67,6 +67,9 @@ _SIGNATURES = {
     "ecc_compute_batch": (ctypes.c_int, [_VP, _I32, ctypes.POINTER(EccImage), _VP, _VP]),
     "ecc_compute_stream": (ctypes.c_int, [_VP, ctypes.POINTER(EccImage), _VP, _I64, _VP]),
     "ecc_compute_levels": (ctypes.c_int, [_VP, ctypes.POINTER(EccImage), _VP, _I32, _VP, _VP]),
+    "ecc_levels_present": (ctypes.c_int, [_VP, ctypes.POINTER(EccImage), _VP, _I32, _VP, _VP]),
+    "ecc_compute_present": (ctypes.c_int, [_VP, ctypes.POINTER(EccImage), _VP, _I32, ctypes.POINTER(_I32), _VP,
+                                           _VP]),
     "ecc_compute_nd": (ctypes.c_int, [_VP, ctypes.POINTER(EccImageNd), _VP, _VP, _VP]),
     "ecc_pipeline_gaussian": (ctypes.c_int, [_VP, ctypes.POINTER(EccImage), _VP, _I32, _I32, _VP, _I32, _VP, _VP]),
     "ecc_compute_noalloc": (ctypes.c_int, [ctypes.POINTER(EccImage), _I32, _I32, _I32, ctypes.c_uint32, _VP, _VP,
@@ -284,6 +287,48 @@ def ecc_compute_levels(plan: Plan, image, levels, out=None, stream=None):
     _check(library().ecc_compute_levels(plan.handle, ctypes.byref(d), levels.data_ptr(), m, out.data_ptr(),
                                         _stream_handle(stream)))
     return out
+
+
+def _f32_image_desc(image):
+    import torch
+    if not isinstance(image, torch.Tensor) or image.dtype != torch.float32 or not image.is_cuda:
+        raise TypeError("the image must be a float32 CUDA tensor")
+    return _desc(image.data_ptr(), image.dim(), ECC_F32, tuple(image.shape), tuple(image.stride()), 4)
+
+
+def ecc_levels_present(plan: Plan, image, max_levels: int = 65536, levels_out=None, count_out=None, stream=None):
+    """Eq. 1's thresholds of a float32 CUDA image (its distinct values, ascending;
+    NaN left out, -0.0 as 0.0), on the device.  Returns (levels, count): a float32
+    CUDA tensor of max_levels entries whose first n hold the levels, and an int32
+    CUDA tensor of one entry holding n (max_levels + 1 when there are more).
+    Asynchronous."""
+    import torch
+    d = _f32_image_desc(image)
+    if levels_out is None:
+        levels_out = torch.empty(max_levels, dtype=torch.float32, device=image.device)
+    if count_out is None:
+        count_out = torch.empty(1, dtype=torch.int32, device=image.device)
+    if levels_out.dtype != torch.float32 or not levels_out.is_contiguous() or levels_out.numel() < max_levels:
+        raise ValueError("levels_out must be a contiguous float32 CUDA tensor of max_levels entries")
+    if count_out.dtype != torch.int32 or count_out.numel() < 1:
+        raise ValueError("count_out must be an int32 CUDA tensor")
+    _check(library().ecc_levels_present(plan.handle, ctypes.byref(d), levels_out.data_ptr(), int(max_levels),
+                                        count_out.data_ptr(), _stream_handle(stream)))
+    return levels_out, count_out
+
+
+def ecc_compute_present(plan: Plan, image, max_levels: int = 65535, stream=None):
+    """The paper's ECC sequence of a float32 CUDA image (Eq. 1 at its distinct
+    values): returns (levels, ecc), CUDA tensors of n entries, ecc[i] =
+    chi(K_{<= levels[i]}).  Synchronizes the stream once, to read n."""
+    import torch
+    d = _f32_image_desc(image)
+    levels = torch.empty(max_levels, dtype=torch.float32, device=image.device)
+    out = torch.empty(max_levels, dtype=torch.int64, device=image.device)
+    n = ctypes.c_int32(0)
+    _check(library().ecc_compute_present(plan.handle, ctypes.byref(d), levels.data_ptr(), int(max_levels),
+                                         ctypes.byref(n), out.data_ptr(), _stream_handle(stream)))
+    return levels[:n.value], out[:n.value]
 
 
 def ecc_compute_nd(plan: Plan, image, out=None, vcec_out=None, stream=None):

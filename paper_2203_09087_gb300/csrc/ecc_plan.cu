@@ -94,7 +94,6 @@ ecc_status ecc_plan_s::ensure_ring(int64_t bytes)
     }
     if ((size_t)bytes > ring_bytes) {
         if (ring) cudaFree(ring);
-    if (aux) cudaFree(aux);
         ring = nullptr;
         ring_bytes = 0;
         cudaError_t e = cudaMalloc(&ring, (size_t)bytes);
@@ -125,6 +124,23 @@ ecc_status ecc_plan_s::ensure_aux(int64_t bytes)
     return ECC_OK;
 }
 
+ecc_status ecc_plan_s::ensure_present(int64_t bytes)
+{
+    if ((size_t)bytes > present_bytes) {
+        if (present) cudaFree(present);
+        present = nullptr;
+        present_bytes = 0;
+        cudaError_t e = cudaMalloc(&present, (size_t)bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            set_error("ecc_levels_present: table allocation failed");
+            return ECC_E_NOMEM;
+        }
+        present_bytes = (size_t)bytes;
+    }
+    return ECC_OK;
+}
+
 void ecc_plan_s::release()
 {
     if (pipe_exec) {
@@ -139,6 +155,7 @@ void ecc_plan_s::release()
     if (stage) cudaFree(stage);
     if (ring) cudaFree(ring);
     if (aux) cudaFree(aux);
+    if (present) cudaFree(present);
     if (stage_ecc) cudaFree(stage_ecc);
     for (int i = 0; i < kRing; ++i) {
         if (ring_copied[i]) cudaEventDestroy(ring_copied[i]);
@@ -156,6 +173,8 @@ void ecc_plan_s::release()
     ring_bytes = 0;
     aux = nullptr;
     aux_bytes = 0;
+    present = nullptr;
+    present_bytes = 0;
     stage_ecc = nullptr;
     copy_stream = nullptr;
 }

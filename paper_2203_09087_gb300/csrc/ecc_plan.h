@@ -53,6 +53,10 @@ struct ecc_plan_s {
     // float32 scratch image of the smoothing pipeline, allocated on first use
     void *aux = nullptr;
     size_t aux_bytes = 0;
+    // present-value thresholds (ecc_levels_present): hash table, key list
+    // and counters, allocated on first use
+    void *present = nullptr;
+    size_t present_bytes = 0;
     // the smoothing pipeline's captured round (kept until its launches finish)
     cudaGraphExec_t pipe_exec = nullptr;
     cudaEvent_t pipe_done = nullptr;
@@ -74,6 +78,7 @@ struct ecc_plan_s {
     ecc_status ensure_stage(int64_t bytes);
     ecc_status ensure_ring(int64_t bytes);
     ecc_status ensure_aux(int64_t bytes);
+    ecc_status ensure_present(int64_t bytes);
     int tune_param(const ecc::Geom &g) const;
     ecc::ScanWs scan_ws() const
     {

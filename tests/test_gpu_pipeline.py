@@ -160,3 +160,28 @@ def test_fused_paper_size_1024_square_255_levels():
     want, final = oracle.gaussian_pipeline(img, taps, levels.astype(np.float64), 11, "vertex", threads=16)
     assert np.array_equal(got, want)
     assert np.array_equal(t.cpu().numpy(), final)
+
+
+def test_one_plan_pipeline_then_out_of_core_then_pipeline():
+    """A plan that grows its out-of-core chunk buffers between two pipeline
+    calls keeps its pipeline scratch image: both pipeline calls and the
+    streamed ECC are exact."""
+    ecc = ecc_mod()
+    rng = np.random.default_rng(64)
+    img = rng.normal(size=(200, 180)).astype(np.float32)
+    taps = ecc.gaussian_taps(1.5)
+    levels = _levels(img, 300)
+    plan = ecc.ecc_plan("u16", 0, 300, max_voxels=1 << 22)
+    lv = torch.from_numpy(levels).cuda()
+    want, _ = oracle.gaussian_pipeline(img, taps, levels.astype(np.float64), 2, "vertex")
+    t = torch.from_numpy(img.copy()).cuda()
+    got = ecc.ecc_pipeline_gaussian(plan, t, taps, 2, lv)
+    ecc.ecc_status_get(plan)
+    assert np.array_equal(got.cpu().numpy(), want)
+    vol = rng.integers(0, 301, size=(40, 64, 96)).astype(np.uint16)
+    streamed = ecc.ecc_compute_stream(plan, vol, device_budget_bytes=1 << 20)
+    assert np.array_equal(streamed, oracle.ecc(vol, 0, 300))
+    t = torch.from_numpy(img.copy()).cuda()
+    got = ecc.ecc_pipeline_gaussian(plan, t, taps, 2, lv)
+    ecc.ecc_status_get(plan)
+    assert np.array_equal(got.cpu().numpy(), want)
