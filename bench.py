@@ -328,6 +328,35 @@ def time_c1(reps: int):
     return {"workload": "256x256 uint8 uniform [0,255], seed 0, 256 bins", "device_us_p50": float(np.median(ts))}
 
 
+def time_pipe(side: int, rounds: int):
+    """The smoothing pipeline on a side^2 float32 field (sigma 3, seed 5) at
+    255 levels (the fused round): four warm-up rounds, then `rounds` timed
+    rounds in one call (CUDA events)."""
+    import torch
+
+    import paper_2203_09087_gb300 as ecc
+    import synth
+    g = torch.Generator(device="cuda")
+    g.manual_seed(5)
+    base = synth.smooth(torch.randn((side, side), generator=g, device="cuda"), 3.0).contiguous()
+    levels = torch.linspace(float(base.min()), float(base.max()), 255, device="cuda").float().contiguous()
+    plan = ecc.ecc_plan("u16", 0, 255, max_voxels=base.numel())
+    taps = ecc.gaussian_taps(2.0)
+    img = base.clone()
+    ecc.ecc_pipeline_gaussian(plan, img, taps, 4, levels)
+    ecc.ecc_status_get(plan)
+    img.copy_(base)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record()
+    res = ecc.ecc_pipeline_gaussian(plan, img, taps, rounds, levels)
+    b.record()
+    torch.cuda.synchronize()
+    ecc.ecc_status_get(plan)
+    assert int(res[0, -1].item()) == 1
+    return {"workload": f"{side}^2 float32 field, 13 taps, 255 levels", "us_per_round": a.elapsed_time(b) * 1e3 / rounds}
+
+
 def time_c4_part(part: str, reps: int):
     """The uneven batch (or only its 2D or 3D images) through one batched call:
     one untimed call, then `reps` timed calls (CUDA events on the stream,
@@ -849,6 +878,9 @@ def main():
                     help="profiler runs: only the 1024^3 uint16 volume (three calls after the checked one)")
     ap.add_argument("--only-c1", action="store_true",
                     help="profiler runs: only the 256^2 uint8 image (ten calls after the checked one)")
+    ap.add_argument("--only-pipe", type=int, default=0, metavar="SIDE",
+                    help="profiler runs: only the smoothing pipeline on a SIDE^2 field at 255 levels (four "
+                         "warm-up rounds, then four timed rounds)")
     ap.add_argument("--only-c4", default=None, choices=["all", "2d", "3d"],
                     help="profiler runs: only the uneven batch, or its 2D or 3D images (three calls after "
                          "the checked one)")
@@ -881,6 +913,9 @@ def main():
         return
     if args.only_c4:
         print(json.dumps(time_c4_part(args.only_c4, reps=3)))
+        return
+    if args.only_pipe:
+        print(json.dumps(time_pipe(args.only_pipe, rounds=4)))
         return
 
     import numpy as np

@@ -189,12 +189,13 @@ __global__ void __launch_bounds__(kFusedThreads) fused_round2d_kernel(const Fuse
     const int x0 = (int)(blockIdx.x % a.tiles_x) * kFTX, y0 = (int)(blockIdx.x / a.tiles_x) * kFTY;
 
     // 1. the float tile, reflected at the image border (Sec. 4's filter):
-    //    a warp per two rows, lanes along them, every load of the two rows
+    //    a warp per four rows, lanes along them, every load of the four rows
     //    issued before the first store (FW <= 152: at most 5 per row)
-    for (int ty = 2 * warp; ty < FH; ty += 2 * (kFusedThreads / 32)) {
-        float v[2][5];
+    constexpr int kRowsIn = 4;
+    for (int ty = kRowsIn * warp; ty < FH; ty += kRowsIn * (kFusedThreads / 32)) {
+        float v[kRowsIn][5];
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
+        for (int h = 0; h < kRowsIn; ++h) {
             const int yy = ty + h < FH ? ty + h : ty;
             const float *srow = src + (int64_t)reflect32(y0 - R + yy, a.ny) * src_sy;
 #pragma unroll
@@ -204,7 +205,7 @@ __global__ void __launch_bounds__(kFusedThreads) fused_round2d_kernel(const Fuse
             }
         }
 #pragma unroll
-        for (int h = 0; h < 2; ++h)
+        for (int h = 0; h < kRowsIn; ++h)
 #pragma unroll
             for (int j = 0; j < 5; ++j) {
                 const int tx = lane + 32 * j;
@@ -216,11 +217,23 @@ __global__ void __launch_bounds__(kFusedThreads) fused_round2d_kernel(const Fuse
     //    (window w holds tile columns 30w-1 .. 30w+30) so a lane reads its
     //    window with two aligned 16-byte loads; pixels outside the image are
     //    missing to the walker, their index is never read as a value
-    for (int i = tid; i < (kFTY + 2) * 128; i += kFusedThreads) {
-        const int qy = i >> 7, w = (i >> 5) & 3, j = i & 31;
-        const int ty = qy - 1, tx = 30 * w - 1 + j;
-        const float v = ftile[(ty + R) * FW + tx + R];
-        qbuf[i] = (unsigned char)lv::lower_bound_count<8, false>(tree, a.m, v);
+    //    (four searches per thread at a time: each is a chain of 8
+    //    dependent shared loads, so independent chains hide one another)
+    constexpr int kQ = (kFTY + 2) * 128, kQU = 4;
+    for (int i0 = tid; i0 < kQ; i0 += kQU * kFusedThreads) {
+        float v[kQU];
+#pragma unroll
+        for (int u = 0; u < kQU; ++u) {
+            const int i = i0 + u * kFusedThreads;
+            const int qy = i >> 7, w = (i >> 5) & 3, j = i & 31;
+            v[u] = i < kQ ? ftile[(qy - 1 + R) * FW + 30 * w - 1 + j + R] : 0.0f;
+        }
+        int q[kQU];
+#pragma unroll
+        for (int u = 0; u < kQU; ++u) q[u] = lv::lower_bound_count<8, false>(tree, a.m, v[u]);
+#pragma unroll
+        for (int u = 0; u < kQU; ++u)
+            if (i0 + u * kFusedThreads < kQ) qbuf[i0 + u * kFusedThreads] = (unsigned char)q[u];
     }
     // 3. the x pass over rows -r .. kFTY + r - 1 of the tile; with the taps
     //    known, a thread makes 4 neighbouring outputs from 3 + NT loaded
