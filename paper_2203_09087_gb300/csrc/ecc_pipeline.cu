@@ -116,8 +116,10 @@ __global__ void __launch_bounds__(256) store_row(const long long *stage, int64_t
 // next round which buffer holds its image.  HBM traffic per round: the
 // image read once plus the halo, and written once.
 constexpr int kFTX = 120;             // output columns per tile (4 windows of 30)
-constexpr int kFTY = 64;              // output rows per tile (8 chunks of 8)
+constexpr int kFTY = 64;              // output rows per tile
 constexpr int kFusedThreads = 256;
+constexpr int kStencilWarps = 2;                         // warps counting cells while the others filter
+constexpr int kChunkRows = kFTY / (8 * kStencilWarps);   // rows a stencil lane walks (4 windows x chunks)
 
 struct FusedArgs {
     float *img, *tmp;                 // the image and the plan's scratch image
@@ -261,13 +263,14 @@ __global__ void __launch_bounds__(kFusedThreads) fused_round2d_kernel(const Fuse
         }
     }
     __syncthreads();
-    if (warp == 0) {
-        // 4. the cell count of this round's image (warp 0)
-        const int w = lane & 3, c = lane >> 2;
+    if (warp < kStencilWarps) {
+        // 4. the cell count of this round's image (the first kStencilWarps
+        //    warps; lane l of them walks window l mod 4 of row chunk l / 4)
+        const int w = lane & 3, c = (warp * 32 + lane) >> 2;
         const int64_t xw = (int64_t)x0 + 30 * w - 1;          // image column of window bit 0
         const uint32_t xex = walk::x_exist_mask(xw, a.nx);
         const uint32_t out_x = xex & 0x7ffffffeu;
-        const int yb = y0 + 8 * c, ye = yb + 8;                // output rows [yb, ye)
+        const int yb = y0 + kChunkRows * c, ye = yb + kChunkRows;  // output rows [yb, ye)
         const walk::Bins bins{hist, a.acc, 0, a.nbins, 0, a.status};
         const walk3::Mul mu = walk3::make_mul();
         // row gy as 8 planes and the existence plane (rows outside the
@@ -292,11 +295,11 @@ __global__ void __launch_bounds__(kFusedThreads) fused_round2d_kernel(const Fuse
             });
         }
     } else {
-        // 5. the y pass, written to the other buffer (warps 1..7); with the
+        // 5. the y pass, written to the other buffer (the other warps); with the
         //    taps known, 4 outputs down a column per thread
         if constexpr (NT > 0) {
             constexpr int NY = 4, NV = NY + NT - 1;
-            for (int i = tid - 32; i < (kFTY / NY) * kFTX; i += kFusedThreads - 32) {
+            for (int i = tid - 32 * kStencilWarps; i < (kFTY / NY) * kFTX; i += kFusedThreads - 32 * kStencilWarps) {
                 const int oy = (i / kFTX) * NY, ox = i - (i / kFTX) * kFTX;
                 const int gx = x0 + ox;
                 const float *q = hbuf + oy * kFTX + ox;
@@ -313,7 +316,7 @@ __global__ void __launch_bounds__(kFusedThreads) fused_round2d_kernel(const Fuse
                 }
             }
         } else {
-            for (int i = tid - 32; i < kFTY * kFTX; i += kFusedThreads - 32) {
+            for (int i = tid - 32 * kStencilWarps; i < kFTY * kFTX; i += kFusedThreads - 32 * kStencilWarps) {
                 const int oy = i / kFTX, ox = i - oy * kFTX;
                 const int gy = y0 + oy, gx = x0 + ox;
                 if (gy >= a.ny || gx >= a.nx) continue;
