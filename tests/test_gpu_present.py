@@ -127,3 +127,20 @@ def test_repeated_calls_and_a_large_volume():
         lv, e = ecc.ecc_compute_present(plan, t)
         assert np.array_equal(lv.cpu().numpy(), want_lv)
         assert np.array_equal(e.cpu().numpy(), want)
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_an_8bit_plan_for_up_to_255_values(mode):
+    """ecc_compute_present on an ECC_U8 plan (hi = 255): the level indices
+    are bytes."""
+    ecc = ecc_mod()
+    rng = np.random.default_rng(11 + mode)
+    vals = np.sort(rng.normal(size=200)).astype(np.float32)
+    img = _from_values(rng, (33, 45, 70), vals)
+    plan = ecc.ecc_plan("u8", 0, 255, complex_mode=mode, max_voxels=img.size)
+    lv, e = ecc.ecc_compute_present(plan, torch.from_numpy(img).cuda())
+    ecc.ecc_status_get(plan)
+    want_lv = oracle.present_levels(img)
+    assert np.array_equal(lv.cpu().numpy(), want_lv)
+    om = oracle.VERTEX if mode == 0 else oracle.TOPCELL
+    assert np.array_equal(e.cpu().numpy(), oracle.ecc_levels(img, want_lv, om, threads=8))
