@@ -116,10 +116,10 @@ __global__ void __launch_bounds__(256) store_row(const long long *stage, int64_t
 // next round which buffer holds its image.  HBM traffic per round: the
 // image read once plus the halo, and written once.
 constexpr int kFTX = 120;             // output columns per tile (4 windows of 30)
-constexpr int kFTY = 64;              // output rows per tile
+constexpr int kFTYBig = 64;           // output rows per tile (images that fill the GPU)
+constexpr int kFTYSmall = 32;         // output rows per tile when 64-row tiles leave SMs idle
 constexpr int kFusedThreads = 256;
 constexpr int kStencilWarps = 2;                         // warps counting cells while the others filter
-constexpr int kChunkRows = kFTY / (8 * kStencilWarps);   // rows a stencil lane walks (4 windows x chunks)
 
 struct FusedArgs {
     float *img, *tmp;                 // the image and the plan's scratch image
@@ -163,9 +163,10 @@ __device__ __forceinline__ float tap_sum(const Taps &t, const float *q, int stri
     return acc;
 }
 
-template <bool TOP, int NT>
+template <bool TOP, int NT, int kFTY>
 __global__ void __launch_bounds__(kFusedThreads) fused_round2d_kernel(const FusedArgs a, const Taps t)
 {
+    constexpr int kChunkRows = kFTY / (8 * kStencilWarps);  // rows a stencil lane walks (4 windows x chunks)
     extern __shared__ __align__(16) unsigned char fsm[];
     const int r = (NT > 0 ? NT : t.n) / 2, R = r > 0 ? r : 1;  // filter radius, tile halo
     const int FW = kFTX + 2 * R, FH = kFTY + 2 * R;  // float tile with halo
@@ -350,7 +351,7 @@ __global__ void __launch_bounds__(kFusedThreads) fused_round2d_kernel(const Fuse
     }
 }
 
-size_t fused_smem(int ntaps, int nbins)
+size_t fused_smem(int ntaps, int nbins, int kFTY)
 {
     const int r = ntaps / 2, R = r > 0 ? r : 1;
     return sizeof(float) * (size_t)((kFTY + 2 * R) * (kFTX + 2 * R) + (kFTY + 2 * r) * kFTX) +
@@ -405,7 +406,12 @@ extern "C" ecc_status ecc_pipeline_gaussian(ecc_plan_t p, const ecc_image *img, 
     // 2D images with at most 255 levels: one fused kernel per round (the
     // image read once and written once); otherwise the round is the
     // float-threshold path and one filter kernel per axis.
-    const size_t fsmem = fused_smem(ntaps, p->nbins);
+    // tile height: 64 rows, or 32 when 64-row tiles would leave SMs idle
+    // (a round is then as long as one CTA's chain of steps)
+    const int fty = (int64_t)((g.nx + kFTX - 1) / kFTX) * ((g.ny + kFTYBig - 1) / kFTYBig) < 2 * (int64_t)p->num_sms
+                        ? kFTYSmall
+                        : kFTYBig;
+    const size_t fsmem = fused_smem(ntaps, p->nbins, fty);
     const bool fused = g.ndim == 2 && m <= 255 && p->nbins <= 4096 && fsmem <= 220 * 1024 &&
                        g.nx <= (int64_t(1) << 30) && g.ny <= (int64_t(1) << 30);
     FusedArgs fa{};
@@ -428,16 +434,21 @@ extern "C" ecc_status ecc_pipeline_gaussian(ecc_plan_t p, const ecc_image *img, 
         fa.status = p->status;
         fa.tiles_x = (int32_t)((g.nx + kFTX - 1) / kFTX);
         if (fsmem > 48 * 1024) {
-            const void *fns[4] = {(const void *)fused_round2d_kernel<false, 0>, (const void *)fused_round2d_kernel<true, 0>,
-                                  (const void *)fused_round2d_kernel<false, 13>,
-                                  (const void *)fused_round2d_kernel<true, 13>};
+            const void *fns[8] = {(const void *)fused_round2d_kernel<false, 0, kFTYBig>,
+                                  (const void *)fused_round2d_kernel<true, 0, kFTYBig>,
+                                  (const void *)fused_round2d_kernel<false, 13, kFTYBig>,
+                                  (const void *)fused_round2d_kernel<true, 13, kFTYBig>,
+                                  (const void *)fused_round2d_kernel<false, 0, kFTYSmall>,
+                                  (const void *)fused_round2d_kernel<true, 0, kFTYSmall>,
+                                  (const void *)fused_round2d_kernel<false, 13, kFTYSmall>,
+                                  (const void *)fused_round2d_kernel<true, 13, kFTYSmall>};
             for (const void *fn : fns) {
                 cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsmem);
                 if (e != cudaSuccess) return cuda_fail(e, "ecc_pipeline_gaussian: fused kernel attributes");
             }
         }
     }
-    const int64_t fused_tiles = fused ? (int64_t)fa.tiles_x * ((g.ny + kFTY - 1) / kFTY) : 0;
+    const int64_t fused_tiles = fused ? (int64_t)fa.tiles_x * ((g.ny + fty - 1) / fty) : 0;
 
     // One round -- ECC at the levels, its row stored, the filter passes --
     // captured once on the plan's side stream and launched `iterations`
@@ -447,16 +458,17 @@ extern "C" ecc_status ecc_pipeline_gaussian(ecc_plan_t p, const ecc_image *img, 
         if (fused) {
             // the paper's 13-tap filter with its taps unrolled, any other width looped
             const dim3 grid((unsigned)fused_tiles);
-            if (ntaps == 13) {
-                if (top)
-                    fused_round2d_kernel<true, 13><<<grid, kFusedThreads, fsmem, cs>>>(fa, t);
+            auto go = [&](auto kern) { kern<<<grid, kFusedThreads, fsmem, cs>>>(fa, t); };
+            if (fty == kFTYBig) {
+                if (ntaps == 13)
+                    top ? go(fused_round2d_kernel<true, 13, kFTYBig>) : go(fused_round2d_kernel<false, 13, kFTYBig>);
                 else
-                    fused_round2d_kernel<false, 13><<<grid, kFusedThreads, fsmem, cs>>>(fa, t);
+                    top ? go(fused_round2d_kernel<true, 0, kFTYBig>) : go(fused_round2d_kernel<false, 0, kFTYBig>);
             } else {
-                if (top)
-                    fused_round2d_kernel<true, 0><<<grid, kFusedThreads, fsmem, cs>>>(fa, t);
+                if (ntaps == 13)
+                    top ? go(fused_round2d_kernel<true, 13, kFTYSmall>) : go(fused_round2d_kernel<false, 13, kFTYSmall>);
                 else
-                    fused_round2d_kernel<false, 0><<<grid, kFusedThreads, fsmem, cs>>>(fa, t);
+                    top ? go(fused_round2d_kernel<true, 0, kFTYSmall>) : go(fused_round2d_kernel<false, 0, kFTYSmall>);
             }
             p->last_launches = 1;
             return cudaGetLastError();

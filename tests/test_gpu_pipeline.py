@@ -104,6 +104,10 @@ def test_paper_size_1024_square_grf():
     ((200, 333), 3, 33, 100, "topcell"),   # the widest filter, ragged tiles
     ((1, 300), 2, 5, 17, "vertex"),        # one row
     ((300, 1), 2, 5, 17, "topcell"),       # one column
+    # enough tiles of 64 rows to fill the GPU twice: the 64-row tile (the
+    # smaller images above take 32-row tiles), ragged in both axes
+    ((1350, 2530), 2, 13, 255, "vertex"),
+    ((1350, 2530), 3, 7, 90, "topcell"),
 ])
 def test_fused_rounds_bit_exact(shape, iters, ntaps, m, mode):
     ecc = ecc_mod()
