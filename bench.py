@@ -328,6 +328,36 @@ def time_c1(reps: int):
     return {"workload": "256x256 uint8 uniform [0,255], seed 0, 256 bins", "device_us_p50": float(np.median(ts))}
 
 
+def time_present(reps: int):
+    """ecc_levels_present on the 512^3 float32 field (sigma 4, seed 1) rounded
+    to its 1024 quantile levels: one call checked against torch.unique, then
+    `reps` calls (CUDA events, mean)."""
+    import torch
+
+    import paper_2203_09087_gb300 as ecc
+    import synth
+    g = torch.Generator(device="cuda")
+    g.manual_seed(1)
+    f = synth.smooth(torch.randn((512, 512, 512), generator=g, device="cuda"), 4.0).contiguous()
+    levels = torch.quantile(f.flatten()[::97].float(), torch.linspace(0, 1, 1024, device="cuda")).float()
+    fq = levels[torch.bucketize(f, levels).clamp_(max=1023)].contiguous()
+    del f
+    plan = ecc.ecc_plan("u16", 0, 65535, max_voxels=fq.numel())
+    lv, cnt = ecc.ecc_levels_present(plan, fq, max_levels=4096)
+    want = torch.unique(fq)
+    n = int(cnt.item())
+    assert n == want.numel() and torch.equal(lv[:n], want)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(reps):
+        ecc.ecc_levels_present(plan, fq, max_levels=4096, levels_out=lv, count_out=cnt)
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / reps
+    return {"workload": "512^3 float32 field rounded to 1024 quantile levels", "distinct_values": n, "ms": ms,
+            "gvox_s": fq.numel() / ms / 1e6}
+
+
 def time_pipe(side: int, rounds: int):
     """The smoothing pipeline on a side^2 float32 field (sigma 3, seed 5) at
     255 levels (the fused round): four warm-up rounds, then `rounds` timed
@@ -881,6 +911,9 @@ def main():
     ap.add_argument("--only-pipe", type=int, default=0, metavar="SIDE",
                     help="profiler runs: only the smoothing pipeline on a SIDE^2 field at 255 levels (four "
                          "warm-up rounds, then four timed rounds)")
+    ap.add_argument("--only-present", action="store_true",
+                    help="profiler runs: only ecc_levels_present on the 512^3 field rounded to 1024 levels (one "
+                         "checked call, then three)")
     ap.add_argument("--only-c4", default=None, choices=["all", "2d", "3d"],
                     help="profiler runs: only the uneven batch, or its 2D or 3D images (three calls after "
                          "the checked one)")
@@ -913,6 +946,9 @@ def main():
         return
     if args.only_c4:
         print(json.dumps(time_c4_part(args.only_c4, reps=3)))
+        return
+    if args.only_present:
+        print(json.dumps(time_present(reps=3)))
         return
     if args.only_pipe:
         print(json.dumps(time_pipe(args.only_pipe, rounds=4)))

@@ -7,10 +7,10 @@
 // compares equal to 0.0, so they are one threshold (reported as +0.0).
 //
 //  1. collect_kernel: every voxel's value becomes a 32-bit key whose
-//     unsigned order is the float order.  A lane whose key differs from
-//     the one before it in the row inserts it into a CTA-private
-//     open-addressing table in shared memory (runs of one value cost one
-//     probe).  At the end the CTA flushes
+//     unsigned order is the float order.  A lane walks 4 consecutive
+//     voxels of each 128 of a row and inserts a key into a CTA-private
+//     open-addressing table in shared memory only where it differs from the
+//     last key the lane inserted (runs of one value cost one probe).  At the end the CTA flushes
 //     its distinct keys into one global table.  Images have few distinct
 //     values compared with their voxels (the paper's datasets have 11-1024),
 //     so the global table sees a few thousand inserts per CTA at most.  A
@@ -34,7 +34,7 @@ namespace ecc {
 namespace {
 
 constexpr uint32_t kEmpty = 0xFFFFFFFFu;  // above every key (+infinity is 0xFF800000)
-constexpr int kCollectThreads = 256;
+constexpr int kCollectThreads = 1024;  // large CTAs: fewer flushes of the same keys into the global table
 constexpr int kSmemSlots = 4096;          // per-CTA table, 16 KB
 constexpr int kSmemFill = kSmemSlots / 2;  // inserts after which the CTA goes global
 constexpr int kRankThreads = 256;
@@ -96,7 +96,6 @@ __global__ void __launch_bounds__(kCollectThreads) collect_kernel(const CollectA
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)blockIdx.x * kCollectThreads + threadIdx.x) >> 5;
     const int64_t nwarps = ((int64_t)gridDim.x * kCollectThreads) >> 5;
-    const int64_t nx32 = (a.nx + 31) / 32 * 32;  // the same trip count on every lane
     auto insert = [&](uint32_t k) {
         if (*reinterpret_cast<volatile unsigned int *>(&s_n) < kSmemFill) {
             if (table_insert(stab, kSmemSlots - 1, k) == 1) atomicAdd(&s_n, 1u);
@@ -104,27 +103,40 @@ __global__ void __launch_bounds__(kCollectThreads) collect_kernel(const CollectA
             atomicAdd(a.gcount, 1u);
         }
     };
+    // rows r = warp, warp + nwarps, ... as (z, y) stepped without a division
+    int64_t z = warp / a.ny, y = warp - z * a.ny;
+    const int64_t dz = nwarps / a.ny, dy = nwarps - dz * a.ny;
+    uint32_t last = kEmpty;  // the key this lane inserted last: equal keys in a row skip the table
     for (int64_t r = warp; r < a.rows; r += nwarps) {
-        const int64_t z = r / a.ny, y = r - z * a.ny;
         const float *row = reinterpret_cast<const float *>(a.src + z * a.sp_z + y * a.sp_y);
-        // four values in flight per lane; a voxel is inserted only where its
-        // key differs from the voxel before it in the row (lane l - 1), so a
-        // run of equal values -- the common case in smooth images -- costs
-        // one probe, and the table merges the repeats that are left
-        for (int64_t x = lane; x < nx32; x += 128) {
+        // a lane takes 4 consecutive voxels of each 128, so in a smooth image
+        // a lane sees runs of one value and probes the table once per run
+        for (int64_t x = 4 * lane; x < a.nx; x += 128) {
             float v[4];
+            if (x + 3 < a.nx && (reinterpret_cast<uintptr_t>(row + x) & 15) == 0) {
+                const float4 q = __ldg(reinterpret_cast<const float4 *>(row + x));
+                v[0] = q.x;
+                v[1] = q.y;
+                v[2] = q.z;
+                v[3] = q.w;
+            } else {
 #pragma unroll
-            for (int u = 0; u < 4; ++u) {
-                const int64_t xu = x + 32 * u;
-                v[u] = xu < a.nx ? __ldg(row + xu) : __int_as_float(0x7fc00000);  // NaN past the row
+                for (int u = 0; u < 4; ++u) v[u] = x + u < a.nx ? __ldg(row + x + u) : __int_as_float(0x7fc00000);
             }
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-                const bool valid = v[u] == v[u];
-                const uint32_t k = valid ? key_of(v[u]) : kEmpty;
-                const uint32_t before = __shfl_up_sync(0xffffffffu, k, 1);
-                if (valid && (lane == 0 || before != k)) insert(k);
+                if (v[u] != v[u]) continue;  // NaN (or past the row): no threshold
+                const uint32_t k = key_of(v[u]);
+                if (k == last) continue;
+                last = k;
+                insert(k);
             }
+        }
+        y += dy;
+        z += dz;
+        if (y >= a.ny) {
+            y -= a.ny;
+            ++z;
         }
     }
     __syncthreads();
@@ -227,9 +239,11 @@ ecc_status levels_present(ecc_plan_s *p, const ecc_image *img, float *d_levels, 
     a.gtab = gtab;
     a.gmask = nslots - 1;
     a.gcount = gcount;
-    // one warp per row, at most 8 CTAs of 8 warps per SM
+    // one warp per row, at most 2 CTAs of 32 warps per SM (each CTA flushes
+    // its distinct keys into the global table once, so fewer, larger CTAs
+    // mean fewer probes of the same global slots)
     int64_t ctas = (a.rows + kCollectThreads / 32 - 1) / (kCollectThreads / 32);
-    const int64_t ctas_max = (int64_t)p->num_sms * 8;
+    const int64_t ctas_max = (int64_t)p->num_sms * 2;
     if (ctas > ctas_max) ctas = ctas_max;
     if (ctas < 1) ctas = 1;
     collect_kernel<<<(unsigned)ctas, kCollectThreads, 0, s>>>(a);
