@@ -83,7 +83,6 @@ struct CollectArgs {
     int64_t sp_y, sp_z;    // source pitches (bytes)
     uint32_t *gtab;        // global table, gmask + 1 slots, all kEmpty on entry
     uint32_t gmask;
-    unsigned int *gcount;  // keys inserted into the global table
 };
 
 __global__ void __launch_bounds__(kCollectThreads) collect_kernel(const CollectArgs a)
@@ -99,8 +98,8 @@ __global__ void __launch_bounds__(kCollectThreads) collect_kernel(const CollectA
     auto insert = [&](uint32_t k) {
         if (*reinterpret_cast<volatile unsigned int *>(&s_n) < kSmemFill) {
             if (table_insert(stab, kSmemSlots - 1, k) == 1) atomicAdd(&s_n, 1u);
-        } else if (table_insert(a.gtab, a.gmask, k) == 1) {
-            atomicAdd(a.gcount, 1u);
+        } else {
+            table_insert(a.gtab, a.gmask, k);
         }
     };
     // rows r = warp, warp + nwarps, ... as (z, y) stepped without a division
@@ -142,7 +141,7 @@ __global__ void __launch_bounds__(kCollectThreads) collect_kernel(const CollectA
     __syncthreads();
     for (int i = threadIdx.x; i < kSmemSlots; i += kCollectThreads) {
         const uint32_t k = stab[i];
-        if (k != kEmpty && table_insert(a.gtab, a.gmask, k) == 1) atomicAdd(a.gcount, 1u);
+        if (k != kEmpty) table_insert(a.gtab, a.gmask, k);
     }
 }
 
@@ -184,8 +183,8 @@ __global__ void __launch_bounds__(kRankThreads) rank_kernel(const uint32_t *keys
 }
 
 // Workspace layout in the plan's present buffer: the table (nslots words),
-// the key list (max_levels words), four words (two counters, the count of
-// ecc_compute_present, one spare).
+// the key list (max_levels words), four words (the key count, the count of
+// ecc_compute_present, two spare).
 uint32_t table_slots(int32_t max_levels)
 {
     uint32_t s = 1024;
@@ -218,15 +217,14 @@ ecc_status levels_present(ecc_plan_s *p, const ecc_image *img, float *d_levels, 
     if (st != ECC_OK) return st;
     uint32_t *gtab = static_cast<uint32_t *>(p->present);
     uint32_t *keys = gtab + nslots;
-    unsigned int *gcount = reinterpret_cast<unsigned int *>(keys + max_levels);
-    unsigned int *nkeys = gcount + 1;
-    int32_t *own_count = reinterpret_cast<int32_t *>(gcount + 2);
+    unsigned int *nkeys = reinterpret_cast<unsigned int *>(keys + max_levels);
+    int32_t *own_count = reinterpret_cast<int32_t *>(nkeys + 1);
     if (!d_count) d_count = own_count;
     if (count_word) *count_word = d_count;
     // the table starts empty (compact_kernel empties it again after use;
     // cleared here too so that an interrupted call leaves nothing behind)
     cudaError_t e = cudaMemsetAsync(gtab, 0xFF, tab_bytes, s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(gcount, 0, 2 * sizeof(unsigned int), s);
+    if (e == cudaSuccess) e = cudaMemsetAsync(nkeys, 0, sizeof(unsigned int), s);
     if (e != cudaSuccess) return cuda_fail(e, "ecc_levels_present: clear");
 
     CollectArgs a{};
@@ -238,7 +236,6 @@ ecc_status levels_present(ecc_plan_s *p, const ecc_image *img, float *d_levels, 
     a.sp_z = g.ndim == 3 ? g.pitch_z : g.pitch_y * g.ny;
     a.gtab = gtab;
     a.gmask = nslots - 1;
-    a.gcount = gcount;
     // one warp per row, at most 2 CTAs of 32 warps per SM (each CTA flushes
     // its distinct keys into the global table once, so fewer, larger CTAs
     // mean fewer probes of the same global slots)
