@@ -229,6 +229,10 @@ def test_host_streaming_path(mode):
     assert np.array_equal(ecc.ecc_compute_host(plan, img), _expect(img, 0, 255, mode))
     sub = img[:, 5:80, 3:120]  # pitched host view
     assert np.array_equal(ecc.ecc_compute_host(plan, sub), _expect(np.ascontiguousarray(sub), 0, 255, mode))
+    # a 2D image of several 8 MiB chunks: the 2D stencil on row ranges
+    img2 = synth.smoothed_field((3100, 4100), 3.0, np.uint8, seed=9, device="cpu").numpy()
+    plan2 = ecc.ecc_plan("u8", 0, 255, complex_mode=MODES[mode], max_voxels=img2.size)
+    assert np.array_equal(ecc.ecc_compute_host(plan2, img2), _expect(img2, 0, 255, mode))
 
 
 def test_config1_matches_golden():
