@@ -61,8 +61,8 @@ struct C3 {
     static constexpr int WORDS = 8 * ES;                // 32-bit words of a 32-voxel window
     static constexpr int CHUNKS = 2 * ES + 1;           // 16-byte loads covering a window at any offset
     static constexpr int ROWB = 16 * CHUNKS;            // bytes of a staged row (odd number of 16-byte units)
-    static constexpr int D = ES == 1 ? 2 : 1;
-    static constexpr int S = ES == 1 ? 3 : 4;
+    static constexpr int D = 2;                         // uint16: 2 x 2 measured 2 % faster than 1 x 4
+    static constexpr int S = ES == 1 ? 3 : 2;
     static constexpr int PLANE = 32 * ROWB;
     static constexpr int STAGE = D * PLANE;             // multiple of 128 bytes
 };
