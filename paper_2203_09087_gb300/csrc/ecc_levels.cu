@@ -28,6 +28,7 @@ namespace ecc {
 namespace {
 
 constexpr int kQuantThreads = 256;
+constexpr int kInFlight = 8;  // voxels a lane searches at once
 
 struct QuantArgs {
     const unsigned char *src;
@@ -69,14 +70,14 @@ __global__ void __launch_bounds__(kQuantThreads, 4) quantize_kernel(const QuantA
         OutT *out = reinterpret_cast<OutT *>(a.dst + z * a.dp_z + y * a.dp_y);
         int x = lane;
         const int nx = (int)a.nx;
-        // four voxels in flight per lane
-        for (; x + 96 < nx; x += 128) {
-            const float v0 = __ldg(row + x), v1 = __ldg(row + x + 32), v2 = __ldg(row + x + 64),
-                        v3 = __ldg(row + x + 96);
-            out[x] = (OutT)lower_bound_count<L, GLOBAL>(lv, a.m, v0);
-            out[x + 32] = (OutT)lower_bound_count<L, GLOBAL>(lv, a.m, v1);
-            out[x + 64] = (OutT)lower_bound_count<L, GLOBAL>(lv, a.m, v2);
-            out[x + 96] = (OutT)lower_bound_count<L, GLOBAL>(lv, a.m, v3);
+        // kInFlight voxels per lane at once: their loads and their searches
+        // (chains of L dependent shared loads) overlap
+        for (; x + 32 * (kInFlight - 1) < nx; x += 32 * kInFlight) {
+            float v[kInFlight];
+#pragma unroll
+            for (int u = 0; u < kInFlight; ++u) v[u] = __ldg(row + x + 32 * u);
+#pragma unroll
+            for (int u = 0; u < kInFlight; ++u) out[x + 32 * u] = (OutT)lower_bound_count<L, GLOBAL>(lv, a.m, v[u]);
         }
         for (; x < nx; x += 32) out[x] = (OutT)lower_bound_count<L, GLOBAL>(lv, a.m, __ldg(row + x));
     }
