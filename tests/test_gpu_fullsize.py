@@ -54,3 +54,16 @@ def test_config2_topcell_matches_oracle_on_a_slab():
     got = _ecc_gpu(slab, 0, 255, mode=1)
     want = oracle.ecc_from_vcec(oracle.vcec_parallel(slab.cpu().numpy(), 0, 255, oracle.TOPCELL))
     assert np.array_equal(got, want)
+
+
+def test_largest_2d_image_16384_square():
+    """The 2D stencil at 16384^2 uint8 (a smoothed field, sigma 3): long
+    row chunks across many warps, against the slab-parallel oracle."""
+    import synth
+    img = synth.smoothed_field((16384, 16384), 3.0, "u8", seed=9, device="cuda")
+    got = _ecc_gpu(img, 0, 255)
+    host = img.cpu().numpy()
+    del img
+    want = oracle.ecc_from_vcec(oracle.vcec_parallel(host, 0, 255, oracle.VERTEX, threads=os.cpu_count()))
+    assert np.array_equal(got, want)
+    assert got[-1] == 1
