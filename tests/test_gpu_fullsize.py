@@ -67,3 +67,18 @@ def test_largest_2d_image_16384_square():
     want = oracle.ecc_from_vcec(oracle.vcec_parallel(host, 0, 255, oracle.VERTEX, threads=os.cpu_count()))
     assert np.array_equal(got, want)
     assert got[-1] == 1
+
+
+def test_1024cube_u8_smooth():
+    """The 8-bit 3D stencil at 1024^3 (1 GiB, eight times the benchmark's
+    volume): TMA coordinates past 512 and the launcher's z-chunk choice at
+    that depth, against the slab-parallel oracle."""
+    import synth
+    vol = synth.smoothed_field((1024, 1024, 1024), 4.0, "u8", seed=12, device="cuda")
+    got = _ecc_gpu(vol, 0, 255)
+    host = vol.cpu().numpy()
+    del vol
+    torch.cuda.empty_cache()
+    want = oracle.ecc_from_vcec(oracle.vcec_parallel(host, 0, 255, oracle.VERTEX, threads=os.cpu_count()))
+    assert np.array_equal(got, want)
+    assert got[-1] == 1
