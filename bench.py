@@ -837,6 +837,10 @@ def run_serving(args):
 
     def serve(replay_rate: bool):
         srv = ecc.ecc_server_create(120 << 30, n_streams=4, max_batch=64)
+        # start-up: the plans of the two job keys on every slot (workspace,
+        # autotuning, batch graph), before the first request arrives
+        ecc.ecc_server_prepare(srv, "u8", 0, 255)
+        ecc.ecc_server_prepare(srv, "u16", 0, 65535)
         outs = [np.zeros(hi + 1, np.int64) for _, hi in views]
         tickets = [0] * len(views)
         t0 = time.perf_counter()

@@ -375,6 +375,14 @@ typedef struct ecc_server_desc {
 /* Creates the server and its scheduler thread on the current device. */
 ecc_status ecc_server_create(ecc_server_t *out, const ecc_server_desc *desc);
 
+/* Makes, on every stream slot, the plan for one job key (dtype, gray range,
+ * complex) with its batch state: workspace allocation, the autotuner's
+ * timing runs and the captured batch graph, which the first job of that key
+ * would otherwise wait for.  Call it at start-up for the keys expected (a
+ * slot busy with a launch is waited for).  Thread-safe.
+ * Errors: ECC_E_INVALID, ECC_E_NOMEM, ECC_E_CUDA, ECC_E_SHUTDOWN. */
+ecc_status ecc_server_prepare(ecc_server_t server, int32_t dtype, int32_t lo, int32_t hi, int32_t complex_mode);
+
 /* Submits one job; thread-safe; returns immediately with *ticket_out.
  *   img   image descriptor; data is a HOST pointer (the server copies it into
  *         a budgeted device buffer at admission) when `host_input` is non-zero,

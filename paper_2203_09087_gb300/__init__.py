@@ -65,6 +65,7 @@ from ._binding import (  # noqa: F401
     ecc_selftest_wait_timeout,
     ecc_server_create,
     ecc_server_destroy,
+    ecc_server_prepare,
     ecc_server_stats,
     ecc_status_get,
     ecc_submit,

@@ -83,6 +83,7 @@ _SIGNATURES = {
     "ecc_submit": (ctypes.c_int, [_VP, ctypes.POINTER(EccImage), _I32, _I32, _I32, _I32, _VP, DONE_FN, _VP,
                                   ctypes.POINTER(_U64)]),
     "ecc_wait": (ctypes.c_int, [_VP, _U64, _I64]),
+    "ecc_server_prepare": (ctypes.c_int, [_VP, _I32, _I32, _I32, _I32]),
     "ecc_server_stats": (ctypes.c_int, [_VP, ctypes.POINTER(ctypes.c_double), _I32, _I32]),
     "ecc_server_destroy": (ctypes.c_int, [_VP, _I32]),
 }
@@ -546,6 +547,11 @@ def ecc_server_stats(server: Server, reset: bool = False) -> dict:
     _check(library().ecc_server_stats(server.handle, vals, 8, int(reset)))
     keys = ["jobs", "voxels", "p50_us", "p99_us", "max_us", "launches", "busy_us", "peak_bytes"]
     return dict(zip(keys, list(vals)))
+
+
+def ecc_server_prepare(server: Server, dtype, lo: int, hi: int, complex_mode: int = ECC_VERTEX_MAX):
+    """Make the plans (and batch graphs) of one job key on every slot ahead of its first jobs."""
+    _check(library().ecc_server_prepare(server.handle, _dtype_code(dtype), int(lo), int(hi), int(complex_mode)))
 
 
 def ecc_server_destroy(server: Server, cancel: bool = False):

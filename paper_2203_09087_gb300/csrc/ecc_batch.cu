@@ -585,6 +585,10 @@ cudaError_t launch_batch_single(ecc_plan_s *p, const Geom &g, const HistDst &h, 
     return e;
 }
 
+// The batch state of a plan (work-list buffers, staging, the captured
+// graph) made ahead of its first batched call.
+ecc_status prepare_batch(ecc_plan_s *p) { return ensure_batch(p); }
+
 void release_batch(ecc_plan_s *p)
 {
     BatchState *b = p->batch;

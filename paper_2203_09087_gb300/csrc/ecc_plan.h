@@ -93,6 +93,7 @@ ecc_status image_geom(const ecc_image *img, int32_t want_dtype, int64_t max_voxe
 cudaError_t launch_stencil(ecc_plan_s *p, const Geom &g, int64_t ob, int64_t oe, const HistDst &h,
                            cudaStream_t s, FusedScan *fs = nullptr);
 void release_batch(ecc_plan_s *p);
+ecc_status prepare_batch(ecc_plan_s *p);
 cudaError_t launch_batch_single(ecc_plan_s *p, const Geom &g, const HistDst &h, cudaStream_t s);
 
 }  // namespace ecc

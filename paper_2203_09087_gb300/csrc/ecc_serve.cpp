@@ -395,6 +395,44 @@ ecc_status ecc_server_create(ecc_server_t *out, const ecc_server_desc *d)
     return ECC_OK;
 }
 
+ecc_status ecc_server_prepare(ecc_server_t s, int32_t dtype, int32_t lo, int32_t hi, int32_t mode)
+{
+    if (!s) {
+        set_error("ecc_server_prepare: NULL server");
+        return ECC_E_INVALID;
+    }
+    const int32_t maxval = dtype == ECC_U8 ? 255 : 65535;
+    if ((dtype != ECC_U8 && dtype != ECC_U16) || lo < 0 || hi < lo || hi > maxval ||
+        (mode != ECC_VERTEX_MAX && mode != ECC_TOPCELL_MIN)) {
+        set_error("ecc_server_prepare: invalid dtype, gray range or complex");
+        return ECC_E_INVALID;
+    }
+    const Key k{dtype, lo, hi, mode};
+    cudaSetDevice(s->device);
+    for (auto &slot : s->slots) {
+        {
+            // hold the slot while its plan is made: the scheduler and the
+            // completion thread skip a busy slot that has no jobs
+            std::unique_lock<std::mutex> lk(s->mu);
+            while (slot.busy) s->cv_sched.wait_for(lk, std::chrono::milliseconds(1));
+            if (s->stopping) {
+                set_error("ecc_server_prepare: the server is shutting down");
+                return ECC_E_SHUTDOWN;
+            }
+            slot.busy = true;
+        }
+        ecc_plan_t plan = plan_for(slot, k, s->d.max_batch, s->d.flags);
+        ecc_status st = plan ? prepare_batch(plan) : ECC_E_NOMEM;
+        {
+            std::lock_guard<std::mutex> g(s->mu);
+            slot.busy = false;
+            s->cv_sched.notify_all();
+        }
+        if (st != ECC_OK) return st;
+    }
+    return ECC_OK;
+}
+
 ecc_status ecc_submit(ecc_server_t s, const ecc_image *img, int32_t host_input, int32_t lo, int32_t hi,
                       int32_t mode, int64_t *out_ecc, ecc_done_fn done, void *user, uint64_t *ticket_out)
 {

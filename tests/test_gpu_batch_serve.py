@@ -236,3 +236,34 @@ def test_batch_degenerate_and_boundary_shapes(mode):
     om = oracle.VERTEX if mode == 0 else oracle.TOPCELL
     for k, img in enumerate(imgs):
         assert np.array_equal(got[k], oracle.ecc(img, 0, 255, om)), (k, img.shape)
+
+
+def test_prepared_keys_serve_exactly():
+    """ecc_server_prepare makes every slot's plan for a key ahead of its
+    jobs; prepared and unprepared keys then serve alike, exactly."""
+    ecc = ecc_mod()
+    srv = ecc.ecc_server_create(1 << 30, n_streams=3, max_batch=8)
+    try:
+        ecc.ecc_server_prepare(srv, "u8", 0, 255)
+        ecc.ecc_server_prepare(srv, "u16", 1000, 1410, ecc.ECC_TOPCELL_MIN)
+        with pytest.raises(ecc.EccError) as ei:
+            ecc.ecc_server_prepare(srv, "u8", 10, 300)
+        assert ei.value.status == ecc.ECC_E_INVALID
+        rng = np.random.default_rng(77)
+        jobs = []
+        for i in range(24):
+            if i % 3 == 2:
+                img = rng.integers(1000, 1411, size=(9, 20, 31)).astype(np.uint16)
+                lo, hi, mode = 1000, 1410, ecc.ECC_TOPCELL_MIN
+            else:
+                img = rng.integers(0, 256, size=(int(rng.integers(5, 90)), int(rng.integers(5, 90))), dtype=np.uint8)
+                lo, hi, mode = 0, 255, ecc.ECC_VERTEX_MAX
+            out = np.zeros(hi - lo + 1, np.int64)
+            t = ecc.ecc_submit(srv, torch.from_numpy(img).cuda(), lo, hi, mode, out=out)
+            jobs.append((t, img, lo, hi, mode, out))
+        for t, img, lo, hi, mode, out in jobs:
+            assert ecc.ecc_wait(srv, t, 60_000_000) == ecc.ECC_OK
+            om = oracle.VERTEX if mode == ecc.ECC_VERTEX_MAX else oracle.TOPCELL
+            assert np.array_equal(out, oracle.ecc(img, lo, hi, om))
+    finally:
+        ecc.ecc_server_destroy(srv)
