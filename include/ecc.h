@@ -302,9 +302,9 @@ ecc_status ecc_compute_batch(ecc_plan_t plan, int32_t n, const ecc_image *host_d
  * by default, and loading one can take device memory): make that first
  * call at start-up, before any memory pool reserves the device's memory and
  * before any stream capture, or run with CUDA_MODULE_LOADING=EAGER.  A 3D
- * image whose row pitch is not a multiple of 16 bytes takes the
- * one-thread-per-voxel kernel here (same result; ecc_compute takes a faster
- * path from its plan workspace, about 13x faster at 500^3 uint8).  Each call clears what must start
+ * image whose row pitch is not a multiple of 16 bytes takes the batch
+ * kernel, its one-image work list kept in the same array, as ecc_compute
+ * runs it from a plan.  Each call clears what must start
  * at zero; all calls on a device share the array, so calls whose work
  * overlaps on the GPU (other streams, other host threads) race and corrupt
  * each other's results.  Synchronous: returns after the work on `stream`

@@ -585,6 +585,64 @@ cudaError_t launch_batch_single(ecc_plan_s *p, const Geom &g, const HistDst &h, 
     return e;
 }
 
+// launch_batch_single without a plan, for ecc_compute_noalloc: the one-image
+// work list lives in kBatchSingleWsBytes of the caller's scratch (8-byte
+// aligned; nothing allocated), and the grid comes from an occupancy query.
+cudaError_t launch_batch_single_ws(const Geom &g, const HistDst &h, int complex_mode, bool check_values, void *ws,
+                                   unsigned int *status, int num_sms, cudaStream_t s)
+{
+    const bool top = complex_mode == ECC_TOPCELL_MIN;
+    const bool wide = g.esize == 2;
+    const bool smem_hist = (size_t)kBatchWarps * h.nbins * 4 <= 96 * 1024;
+    const size_t smem = smem_hist ? (size_t)kBatchWarps * h.nbins * 4 : 0;
+    void *fn = nullptr;
+    int per_sm = 0;
+    cudaError_t e = wide ? (top ? batch_instance<16, true>(&fn, smem, &per_sm) : batch_instance<16, false>(&fn, smem, &per_sm))
+                         : (top ? batch_instance<8, true>(&fn, smem, &per_sm) : batch_instance<8, false>(&fn, smem, &per_sm));
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorNotSupported;
+    unsigned char *w = static_cast<unsigned char *>(ws);
+    BatchArgs args{};
+    args.hdr = reinterpret_cast<const BatchHeader *>(w);         // 16 bytes
+    args.img = reinterpret_cast<const BatchImage *>(w + 16);     // 64 bytes
+    args.start = reinterpret_cast<long long *>(w + 80);          // 2 words
+    args.order = reinterpret_cast<int *>(w + 96);
+    args.counter = reinterpret_cast<unsigned int *>(w + 100);
+    args.acc = h.acc;
+    args.lo = h.lo;
+    args.nbins = h.nbins;
+    args.chunk2d = 32;
+    args.chunk3d = 16;
+    args.smem_hist = smem_hist;
+    args.range_check = walk::range_is_narrow(h.lo, h.nbins, g.esize);
+    args.check_all = args.range_check && check_values;
+    args.lo_bits = (uint32_t)h.lo;
+    args.hi_bits = (uint32_t)(h.lo + h.nbins - 1);
+    args.mu = walk3::make_mul();
+    args.status = status;
+    const BatchImage im{g.data, g.nx, g.ny, g.nz, g.pitch_y, g.pitch_z, g.ndim, g.esize};
+    init_single<<<1, 1, 0, s>>>(args, im);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) {
+        void *argv[] = {&args};
+        e = cudaLaunchKernel(fn, dim3((unsigned)(num_sms * per_sm)), dim3(kBatchWarps * 32), argv, smem, s);
+    }
+    return e;
+}
+
+cudaError_t preload_batch()
+{
+    const void *fns[] = {(const void *)batch_kernel<8, false>, (const void *)batch_kernel<8, true>,
+                         (const void *)batch_kernel<16, false>, (const void *)batch_kernel<16, true>,
+                         (const void *)init_single};
+    cudaFuncAttributes fa;
+    for (const void *f : fns) {
+        const cudaError_t e = cudaFuncGetAttributes(&fa, f);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
 // The batch state of a plan (work-list buffers, staging, the captured
 // graph) made ahead of its first batched call.
 ecc_status prepare_batch(ecc_plan_s *p) { return ensure_batch(p); }

@@ -23,9 +23,8 @@
 // CUDA_MODULE_LOADING=EAGER).
 //
 // A 3D image whose rows the TMA cannot address (row pitch not a multiple of
-// 16 bytes) takes the one-thread-per-voxel kernel here, where ecc_compute
-// walks it with the batch kernel from its plan workspace; the result is the
-// same, about 13x slower (500^3 uint8: 1.98 ms against 0.15 ms).
+// 16 bytes) goes through the batch kernel with its one-image work list in
+// the scratch array, as ecc_compute runs it from a plan.
 //
 // Every call on a device shares the array: each call clears the parts that
 // must start at zero before using them, and calls whose work overlaps on the
@@ -49,12 +48,14 @@ constexpr int kNoallocTiles = (kNoallocMaxBins + kScanTile - 1) / kScanTile;
 // then 32 words for the status word (32-bit word 0), the two scan counters
 // (words 2, 3) and the stencil's work counters (words 4, 5);
 // then kNoallocTiles words of tile status (ints, 2 per word) rounded up;
-// then 2 * kNoallocTiles words of tile values.
+// then 2 * kNoallocTiles words of tile values;
+// then kBatchWords words for the batch kernel's one-image work list.
 constexpr int kAccWords = kNoallocMaxBins;
 constexpr int kCtlWords = 32;
 constexpr int kStatWords = (kNoallocTiles + 1) / 2;
 constexpr int kValWords = 2 * kNoallocTiles;
-constexpr int kScratchWords = kAccWords + kCtlWords + kStatWords + kValWords;
+constexpr int kBatchWords = (int)(kBatchSingleWsBytes / 8);  // one-image work list of the batch kernel
+constexpr int kScratchWords = kAccWords + kCtlWords + kStatWords + kValWords + kBatchWords;
 
 static __device__ __align__(256) unsigned long long g_noalloc_scratch[kScratchWords];
 
@@ -82,7 +83,8 @@ ecc_status scratch_for_current_device(unsigned long long **out, int *sms)
         e = clear_device_now(p, sizeof(g_noalloc_scratch));
         if (e != cudaSuccess) return cuda_fail(e, "ecc_compute_noalloc: scratch clear");
         if ((e = preload_bs3d()) != cudaSuccess || (e = preload_bs2d()) != cudaSuccess ||
-            (e = preload_direct()) != cudaSuccess || (e = preload_scan()) != cudaSuccess)
+            (e = preload_batch()) != cudaSuccess || (e = preload_direct()) != cudaSuccess ||
+            (e = preload_scan()) != cudaSuccess)
             return cuda_fail(e, "ecc_compute_noalloc: kernel loading");
         int n = 0;
         e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
@@ -148,6 +150,11 @@ extern "C" ecc_status ecc_compute_noalloc(const ecc_image *img, int32_t lo, int3
     e = cudaErrorNotSupported;
     if (!(flags & ECC_FLAG_KERNEL_DIRECT) && bitslice_supported(g))
         e = launch_bitslice(g, 0, outer, h, complex_mode, range, status, ctl + 4, sms, 0, s);
+    // a 3D image whose rows the TMA cannot address: the batch kernel on a
+    // one-image work list in the scratch, as ecc_compute does from its plan
+    if (e == cudaErrorNotSupported && !(flags & ECC_FLAG_KERNEL_DIRECT) && g.ndim == 3)
+        e = launch_batch_single_ws(g, h, complex_mode, range, base + kAccWords + kCtlWords + kStatWords + kValWords,
+                                   status, sms, s);
     if (e == cudaErrorNotSupported) e = launch_direct(g, 0, outer, h, complex_mode, range, status, sms, s);
     if (e != cudaSuccess) return cuda_fail(e, "ecc_compute_noalloc: stencil launch");
     e = launch_scan(acc, reinterpret_cast<long long *>(d_ecc), reinterpret_cast<long long *>(d_vcec), 1,

@@ -94,6 +94,13 @@ cudaError_t launch_stencil(ecc_plan_s *p, const Geom &g, int64_t ob, int64_t oe,
                            cudaStream_t s, FusedScan *fs = nullptr);
 void release_batch(ecc_plan_s *p);
 ecc_status prepare_batch(ecc_plan_s *p);
+// One 3D image through the batch kernel with its work list in caller scratch
+// of kBatchSingleWsBytes (no plan, no allocation); check_values: compare
+// every voxel with [lo, hi] when the range is narrower than the type.
+constexpr size_t kBatchSingleWsBytes = 128;
+cudaError_t launch_batch_single_ws(const Geom &g, const HistDst &h, int complex_mode, bool check_values, void *ws,
+                                   unsigned int *status, int num_sms, cudaStream_t s);
+cudaError_t preload_batch();
 cudaError_t launch_batch_single(ecc_plan_s *p, const Geom &g, const HistDst &h, cudaStream_t s);
 
 }  // namespace ecc

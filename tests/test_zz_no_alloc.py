@@ -54,10 +54,14 @@ def _images(kind):
         a = rng.integers(0, 256, size=(40, 70, 96), dtype=np.uint8)
         b = rng.integers(0, 4, size=(33, 50, 64), dtype=np.uint8)
         return a, b, 0, 255
-    if kind == "3d_u8_unaligned":     # one-thread-per-voxel kernel
+    if kind == "3d_u8_unaligned":     # the batch kernel, its work list in the scratch
         a = rng.integers(0, 256, size=(21, 33, 45), dtype=np.uint8)
         b = rng.integers(0, 9, size=(5, 60, 77), dtype=np.uint8)
         return a, b, 0, 255
+    if kind == "3d_u16_unaligned":    # the same with 16-bit rows of 2 x 37 bytes, a narrow range
+        a = rng.integers(300, 700, size=(14, 29, 37)).astype(np.uint16)
+        b = rng.integers(300, 304, size=(40, 7, 37)).astype(np.uint16)
+        return a, b, 300, 699
     if kind == "2d_u8":
         a = rng.integers(0, 256, size=(300, 517), dtype=np.uint8)
         b = rng.integers(0, 3, size=(64, 2000), dtype=np.uint8)
@@ -70,7 +74,8 @@ def _images(kind):
 
 
 @pytest.mark.parametrize("mode", [0, 1])
-@pytest.mark.parametrize("kind", ["3d_u8_aligned", "3d_u8_unaligned", "2d_u8", "3d_u16_full_range"])
+@pytest.mark.parametrize("kind", ["3d_u8_aligned", "3d_u8_unaligned", "2d_u8", "3d_u16_full_range",
+                                  "3d_u16_unaligned"])
 def test_two_calls_in_a_row_match_ecc_compute(kind, mode):
     a, b, lo, hi = _images(kind)
     ta, tb = torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda()
