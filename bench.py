@@ -16,10 +16,10 @@ Also reported on the same JSON line:
                 back), copies inside the timed region;
   cpu_baseline  the CPU oracle (as it stands) on a bounded slab of the same
                 volume, on all host cores;
-  config1, single_u16, batched, serving
-                the other configurations (C1 latency, C3 1024^3 uint16, C4
-                uneven batch against one launch per image, C5 Poisson serving
-                with p50/p99 and a saturating replay), each with its own
+  latency_256x256, single_u16, batched, serving
+                the other configurations (256^2 uint8 latency, 1024^3 uint16,
+                the uneven 4352-image batch against one launch per image,
+                Poisson serving with p50/p99 and a saturating replay), each with its own
                 timing; --main-only leaves them out, --extras adds the
                 NEXT-row workloads (float thresholds, smoothing pipeline,
                 top-cell and 4D, one-core CPU baselines).
@@ -220,7 +220,7 @@ def run_reference(args):
         return 0
     import synth
     dev = "cuda" if torch.cuda.is_available() else "cpu"
-    vol = synth.config2_smooth_3d(device=dev).cpu().numpy()
+    vol = synth.smooth_3d_512(device=dev).cpu().numpy()
     import oracle
     threads = os.cpu_count() or 1
     # each step: the oracle on a bounded slab (about 10 s of CPU work)
@@ -312,7 +312,7 @@ def time_c1(reps: int):
 
     import paper_2203_09087_gb300 as ecc
     import synth
-    t = torch.from_numpy(synth.config1_uniform_2d()).cuda()
+    t = torch.from_numpy(synth.uniform_2d_256()).cuda()
     plan = ecc.ecc_plan("u8", 0, 255, max_voxels=t.numel())
     out = ecc.ecc_compute(plan, t)
     ecc.ecc_status_get(plan)
@@ -433,7 +433,7 @@ def run_single_u16(args):
 
     import paper_2203_09087_gb300 as ecc
     import synth
-    vol = synth.config3_smooth_blobs_u16(device="cuda")
+    vol = synth.smooth_blobs_u16_1024(device="cuda")
     nvox = vol.numel()
     plan = ecc.ecc_plan("u16", 0, 65535, max_voxels=nvox, flags=ecc.ECC_FLAG_TIME_KERNELS)
     out = torch.empty(65536, dtype=torch.int64, device="cuda")
@@ -494,7 +494,7 @@ def time_c3(reps=3):
 
     import paper_2203_09087_gb300 as ecc
     import synth
-    vol = synth.config3_smooth_blobs_u16(device="cuda")
+    vol = synth.smooth_blobs_u16_1024(device="cuda")
     plan = ecc.ecc_plan("u16", 0, 65535, max_voxels=vol.numel())
     out = torch.empty(65536, dtype=torch.int64, device="cuda")
     ecc.ecc_compute(plan, vol, out)
@@ -507,7 +507,7 @@ def time_c3(reps=3):
     e1.record()
     e1.synchronize()
     ms = e0.elapsed_time(e1) / reps
-    return {"workload": "1024^3 uint16 (C3 input), 65536 bins", "ms_per_call": ms,
+    return {"workload": "1024^3 uint16 smoothed field + 2000 blobs, 65536 bins", "ms_per_call": ms,
             "gvox_s": vol.numel() / ms / 1e6}
 
 
@@ -663,8 +663,8 @@ def run_gaussian_pipeline(args):
                           "and the stencil (2 B/px)"}
 
 
-def run_config1_latency(args):
-    """C1, the 256x256 uint8 uniform image: too small to fill the GPU, so the
+def run_latency_256sq(args):
+    """The 256x256 uint8 uniform image: too small to fill the GPU, so the
     figure is the latency of one ecc_compute call (stencil and scan) measured
     with CUDA events on the stream, median of 200 calls -- on an idle stream
     (launch latency included) and queued behind a spin kernel (the device
@@ -675,7 +675,7 @@ def run_config1_latency(args):
 
     import paper_2203_09087_gb300 as ecc
     import synth
-    img = synth.config1_uniform_2d()
+    img = synth.uniform_2d_256()
     t = torch.from_numpy(img).cuda()
     plan = ecc.ecc_plan("u8", 0, 255, max_voxels=t.numel())
     out = ecc.ecc_compute(plan, t)
@@ -718,26 +718,27 @@ def run_config1_latency(args):
 
 def run_cpu_baselines(args):
     """The CPU oracle (as it stands, one host thread) on the other
-    configurations, each a bounded sample: C1 in full, a slab of planes of
-    the C3 volume (65536 bins), and the first 2D images and first 3D patches
-    of the C4 batch.  Reported baselines, not targets."""
+    configurations, each a bounded sample: the 256^2 image in full, a slab of
+    planes of the 1024^3 uint16 volume (65536 bins), and the first 2D images
+    and first 3D patches of the uneven batch.  Reported baselines, not
+    targets."""
     import numpy as np
 
     import oracle
     import synth
     res = {}
-    img = synth.config1_uniform_2d()
+    img = synth.uniform_2d_256()
     t0 = time.perf_counter()
     oracle.ecc(img, 0, 255, oracle.VERTEX)
     dt = time.perf_counter() - t0
-    res["config1"] = {"value": img.size / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+    res["uniform_256x256"] = {"value": img.size / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
                       "sample": "the whole 256x256 image"}
-    vol = synth.config3_smooth_blobs_u16(device="cuda").cpu().numpy()
+    vol = synth.smooth_blobs_u16_1024(device="cuda").cpu().numpy()
     t0 = time.perf_counter()
     planes = 6
     oracle.vcec_rows(vol, 0, planes, 0, 65535, oracle.VERTEX)
     dt = time.perf_counter() - t0
-    res["config3"] = {"value": planes * vol.shape[1] * vol.shape[2] / dt / 1e9, "unit": UNIT, "cores": 1,
+    res["u16_1024cube_slab"] = {"value": planes * vol.shape[1] * vol.shape[2] / dt / 1e9, "unit": UNIT, "cores": 1,
                       "kind": "oracle", "sample": f"cells based on planes 0..{planes - 1} of the 1024^3 uint16 volume"}
     del vol
     specs = synth.batch_specs()
@@ -750,7 +751,7 @@ def run_cpu_baselines(args):
         oracle.ecc(im, 0, 255, oracle.VERTEX)
     dt = time.perf_counter() - t0
     vox = sum(im.size for im in imgs)
-    res["config4"] = {"value": vox / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
+    res["uneven_batch_first_images"] = {"value": vox / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
                       "sample": f"the first 16 2D images and first 2 3D patches of the batch ({vox} voxels)"}
     return res
 
@@ -766,7 +767,7 @@ def run_topcell_and_4d(args):
 
     import paper_2203_09087_gb300 as ecc
     import synth
-    vol = synth.config2_smooth_3d(device="cuda")
+    vol = synth.smooth_3d_512(device="cuda")
     l2 = torch.cuda.get_device_properties(torch.cuda.current_device()).L2_cache_size
     flush = torch.empty(2 * l2 + (1 << 20), dtype=torch.uint8, device="cuda")
     res = {}
@@ -903,7 +904,7 @@ def main():
     ap.add_argument("--serve-seconds", type=float, default=60.0,
                     help="duration of the serving workload's Poisson request stream (the configuration's 60 s)")
     ap.add_argument("--main-only", action="store_true",
-                    help="only the headline 512^3 workload (no C1/C3/C4/C5 keys)")
+                    help="only the headline 512^3 workload (no keys for the other configurations)")
     ap.add_argument("--quick", action="store_true",
                     help="profiler runs: no one-second warm-up floor, no e2e and CPU legs")
     ap.add_argument("--only-4d", type=int, default=0, metavar="SIDE",
@@ -968,7 +969,7 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     shape = tuple(int(x) for x in args.shape.split(","))
-    vol = synth.config2_smooth_3d(device="cuda", shape=shape)
+    vol = synth.smooth_3d_512(device="cuda", shape=shape)
     nvox = vol.numel()
     # no ECC_FLAG_TIME_KERNELS in the timed plan: its events inside every call
     # cost ~5 us a step; a step of one launch is timed by the step's own events
@@ -1103,10 +1104,10 @@ def main():
         line["cpu_baseline_1core"] = cpu_oracle_sample(host_vol, budget_s=4.0, threads=1)
     if rank == 0 and not args.main_only and not args.quick:
         # the other configurations, each with its own timing
-        line["config1"] = run_config1_latency(args)       # C1: 256^2 uint8 latency
-        line["single_u16"] = run_single_u16(args)        # C3: 1024^3 uint16
-        line["batched"] = run_batched(args)              # C4: uneven batch vs one launch per image
-        line["serving"] = run_serving(args)              # C5: Poisson stream, p50/p99, saturating replay
+        line["latency_256x256"] = run_latency_256sq(args)  # 256^2 uint8 latency
+        line["single_u16"] = run_single_u16(args)        # 1024^3 uint16
+        line["batched"] = run_batched(args)              # uneven batch vs one launch per image
+        line["serving"] = run_serving(args)              # Poisson stream, p50/p99, saturating replay
     if args.extras and rank == 0:
         line["float_levels"] = run_float_levels(args)
         line["gaussian_pipeline"] = run_gaussian_pipeline(args)

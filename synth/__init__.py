@@ -127,17 +127,17 @@ def add_blobs(vol: torch.Tensor, count: int, seed: int, r_range=(3, 12), v_range
 
 # --- the five benchmark configurations ---------------------------------------
 
-def config1_uniform_2d() -> np.ndarray:
+def uniform_2d_256() -> np.ndarray:
     """One 256x256 uint8 image, iid uniform in [0,255], seed 0."""
     return uniform((256, 256), np.uint8, seed=0)
 
 
-def config2_smooth_3d(device="cuda", shape=(512, 512, 512)) -> torch.Tensor:
+def smooth_3d_512(device="cuda", shape=(512, 512, 512)) -> torch.Tensor:
     """512^3 uint8: N(0,1) seed 1 smoothed with sigma=4, rescaled to [0,255]."""
     return smoothed_field(shape, 4.0, np.uint8, seed=1, device=device)
 
 
-def config3_smooth_blobs_u16(device="cuda", shape=(1024, 1024, 1024), blobs: int = 2000) -> torch.Tensor:
+def smooth_blobs_u16_1024(device="cuda", shape=(1024, 1024, 1024), blobs: int = 2000) -> torch.Tensor:
     """1024^3 uint16: N(0,1) seed 2 smoothed with sigma=8, rescaled to [0,65535], plus blobs."""
     v = smoothed_field(shape, 8.0, np.uint16, seed=2, device=device)
     return add_blobs(v, blobs, seed=2)

@@ -18,10 +18,10 @@ import synth  # noqa: E402
 
 
 def main():
-    img = synth.config1_uniform_2d()
+    img = synth.uniform_2d_256()
     for mode in (oracle.VERTEX, oracle.TOPCELL):
         ecc = oracle.ecc(img, 0, 255, mode)
-        path = os.path.join(HERE, f"config1_uniform_256x256_seed0_{mode}.txt")
+        path = os.path.join(HERE, f"uniform_256x256_seed0_{mode}.txt")
         np.savetxt(path, ecc, fmt="%d",
                    header=f"ECC[g] = chi(K_<=g), g=0..255, {mode} complex; 256x256 uint8 "
                           "iid uniform numpy default_rng(0); written by make_golden.py (oracle only)")

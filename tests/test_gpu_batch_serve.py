@@ -88,8 +88,8 @@ def _oracle_many(arrays, his, mode=oracle.VERTEX):
     return out
 
 
-def test_batch_full_size_config4_every_row():
-    """The uneven 4096 + 256 batch at full size (C4): every row equals the
+def test_uneven_batch_4352_images_every_row():
+    """The uneven 4096 + 256 batch at full size: every row equals the
     oracle, and the one-launch-per-image path gives the same rows."""
     import synth
     ecc = ecc_mod()
@@ -108,11 +108,11 @@ def test_batch_full_size_config4_every_row():
     assert not bad, (len(bad), bad[:5])
 
 
-def test_serving_config5_sample_against_oracle():
-    """A seeded sample of 100 requests drawn from the serving workload (C5:
-    the 60 s Poisson list, 2D uint8 128^2-4096^2 and 3D uint8/uint16
-    64^3-768^3, crops of the resident seeded fields) served together under
-    the 120 GB budget: every result equals the oracle."""
+def test_serving_poisson_sample_against_oracle():
+    """A seeded sample of 100 requests drawn from the serving workload (the
+    60 s Poisson list, 2D uint8 128^2-4096^2 and 3D uint8/uint16 64^3-768^3,
+    crops of the resident seeded fields) served together under the 120 GB
+    budget: every result equals the oracle."""
     import synth
     ecc = ecc_mod()
     reqs = synth.poisson_requests(2000.0, 60.0)

@@ -23,9 +23,9 @@ def _ecc_gpu(vol, lo, hi, mode=0):
     return out.cpu().numpy()
 
 
-def test_config2_512cube_u8_smooth():
+def test_512cube_u8_smooth():
     import synth
-    vol = synth.config2_smooth_3d(device="cuda")
+    vol = synth.smooth_3d_512(device="cuda")
     got = _ecc_gpu(vol, 0, 255)
     host = vol.cpu().numpy()
     want = oracle.ecc_from_vcec(oracle.vcec_parallel(host, 0, 255, oracle.VERTEX, threads=os.cpu_count()))
@@ -33,9 +33,9 @@ def test_config2_512cube_u8_smooth():
     assert got[-1] == 1
 
 
-def test_config3_1024cube_u16_blobs():
+def test_1024cube_u16_blobs():
     import synth
-    vol = synth.config3_smooth_blobs_u16(device="cuda")
+    vol = synth.smooth_blobs_u16_1024(device="cuda")
     got = _ecc_gpu(vol, 0, 65535)
     host = vol.cpu().numpy()
     del vol
@@ -45,11 +45,11 @@ def test_config3_1024cube_u16_blobs():
     assert got[-1] == 1
 
 
-def test_config2_topcell_matches_oracle_on_a_slab():
+def test_512cube_topcell_matches_oracle_on_a_slab():
     """Top-cell complex at full size, checked on a slab of planes (chunk
     additivity: the GPU result of the slab as an image equals the oracle's)."""
     import synth
-    vol = synth.config2_smooth_3d(device="cuda")
+    vol = synth.smooth_3d_512(device="cuda")
     slab = vol[100:164].contiguous()
     got = _ecc_gpu(slab, 0, 255, mode=1)
     want = oracle.ecc_from_vcec(oracle.vcec_parallel(slab.cpu().numpy(), 0, 255, oracle.TOPCELL))

@@ -235,12 +235,12 @@ def test_host_streaming_path(mode):
     assert np.array_equal(ecc.ecc_compute_host(plan2, img2), _expect(img2, 0, 255, mode))
 
 
-def test_config1_matches_golden():
+def test_256sq_uniform_matches_golden():
     import synth
     from pathlib import Path
-    img = synth.config1_uniform_2d()
+    img = synth.uniform_2d_256()
     for mode in MODES:
-        want = np.loadtxt(Path(__file__).parent / "golden" / f"config1_uniform_256x256_seed0_{mode}.txt",
+        want = np.loadtxt(Path(__file__).parent / "golden" / f"uniform_256x256_seed0_{mode}.txt",
                           dtype=np.int64)
         for kernel in KERNELS:
             assert np.array_equal(_run(_gpu(img), 0, 255, mode, kernel), want)

@@ -97,7 +97,7 @@ def test_stream_full_size_512cube_against_device_path():
     buffers equals the device-resident ECC."""
     import synth
     ecc = ecc_mod()
-    vol = synth.config2_smooth_3d(device="cuda")
+    vol = synth.smooth_3d_512(device="cuda")
     plan = ecc.ecc_plan("u8", 0, 255, max_voxels=vol.numel())
     want = ecc.ecc_compute(plan, vol).cpu().numpy()
     host = vol.cpu().numpy()
@@ -111,7 +111,7 @@ def test_host_path_many_chunks_against_device_path():
     in 8 MiB chunks) equals the device-resident ECC."""
     import synth
     ecc = ecc_mod()
-    vol = synth.config2_smooth_3d(device="cuda", shape=(600, 512, 512))
+    vol = synth.smooth_3d_512(device="cuda", shape=(600, 512, 512))
     plan = ecc.ecc_plan("u8", 0, 255, max_voxels=vol.numel())
     want = ecc.ecc_compute(plan, vol).cpu().numpy()
     host = vol.cpu().pin_memory().numpy()

@@ -255,13 +255,13 @@ def test_errors():
 
 # ---------------------------------------------------------------- golden file
 
-def test_golden_config1():
+def test_golden_256sq_uniform():
     """The stored ECC of the 256x256 uniform image was written by
     tests/golden/make_golden.py, which calls only the oracle."""
     import synth
-    path = Path(__file__).parent / "golden" / "config1_uniform_256x256_seed0_vertex.txt"
+    path = Path(__file__).parent / "golden" / "uniform_256x256_seed0_vertex.txt"
     want = np.loadtxt(path, dtype=np.int64)
-    img = synth.config1_uniform_2d()
+    img = synth.uniform_2d_256()
     assert np.array_equal(oracle.ecc(img, 0, 255, oracle.VERTEX), want)
     # the same image checked independently at a few thresholds by flood fill
     for t in (0, 37, 128, 200, 255):
