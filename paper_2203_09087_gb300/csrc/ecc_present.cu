@@ -10,11 +10,12 @@
 //     unsigned order is the float order.  A lane walks 4 consecutive
 //     voxels of each 128 of a row and inserts a key into a CTA-private
 //     open-addressing table in shared memory only where it differs from the
-//     last key the lane inserted (runs of one value cost one probe).  At the end the CTA flushes
-//     its distinct keys into one global table.  Images have few distinct
-//     values compared with their voxels (the paper's datasets have 11-1024),
-//     so the global table sees a few thousand inserts per CTA at most.  A
-//     CTA whose shared table fills sends the rest straight to the global one.
+//     last key the lane inserted (runs of one value cost one probe).  At the
+//     end the CTA flushes its distinct keys into one global table.  Images
+//     have few distinct values compared with their voxels (the paper's
+//     datasets have 11-1024), so the global table sees a few thousand
+//     inserts per CTA at most.  A CTA whose shared table passes half full
+//     sends the rest straight to the global one.
 //  2. compact_kernel: the global table's keys are gathered into a list
 //     (any order), and the slots are reset for the next call.
 //  3. rank_kernel: each key's rank is the number of smaller keys (keys are
