@@ -14,6 +14,8 @@
 // tuned once.  ECC_FLAG_NO_AUTOTUNE (or ECC_TUNE=off) keeps the defaults.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -191,30 +193,43 @@ void ecc_plan_s::autotune()
         save_choice(key + "|3dw", c);
     }
     if (needb) {
-        // batched kernel on an uneven synthetic batch (2D and 3D images in one buffer)
+        // batched kernel on an uneven synthetic batch (2D and 3D images in one
+        // buffer): sides spread over 64-1024 (2D) and 32-252 (3D), enough
+        // images to fill the GPU several times over, so the chunk lengths
+        // are judged on load balance and halo cost rather than launch
+        // latency; the small mix of the first version when the plan cannot
+        // hold that many voxels
         std::vector<ecc_image> imgs;
         std::vector<int64_t> offs;
         int64_t total = 0;
-        const int n2 = d.max_images >= 48 ? 40 : d.max_images / 2 + 1;
-        const int n3 = d.max_images - n2 >= 8 ? 8 : d.max_images - n2;
-        for (int i = 0; i < n2 + n3; ++i) {
-            ecc_image im{};
-            im.dtype = d.dtype;
-            if (i < n2) {
-                im.ndim = 2;
-                im.dims[0] = 100 + 37 * i % 400;
-                im.dims[1] = 150 + 53 * i % 500;
-                offs.push_back(total);
-                total += im.dims[0] * im.dims[1];
-            } else {
-                const int64_t sd = 48 + 16 * ((i - n2) % 5);
-                im.ndim = 3;
-                im.dims[0] = im.dims[1] = im.dims[2] = sd;
-                offs.push_back(total);
-                total += sd * sd * sd;
+        auto make = [&](bool big) {
+            imgs.clear();
+            offs.clear();
+            total = 0;
+            const int n2 = big ? std::min(192, d.max_images * 3 / 4 + 1)
+                               : (d.max_images >= 48 ? 40 : d.max_images / 2 + 1);
+            const int n3 = std::max(0, std::min(big ? 24 : 8, d.max_images - n2));
+            for (int i = 0; i < n2 + n3; ++i) {
+                ecc_image im{};
+                im.dtype = d.dtype;
+                if (i < n2) {
+                    im.ndim = 2;
+                    im.dims[0] = big ? 64 + (97 * i) % 961 : 100 + 37 * i % 400;
+                    im.dims[1] = big ? 64 + (61 * i + 300) % 961 : 150 + 53 * i % 500;
+                    offs.push_back(total);
+                    total += im.dims[0] * im.dims[1];
+                } else {
+                    const int64_t sd = big ? 32 + 10 * ((7 * (i - n2)) % 23) : 48 + 16 * ((i - n2) % 5);
+                    im.ndim = 3;
+                    im.dims[0] = im.dims[1] = im.dims[2] = sd;
+                    offs.push_back(total);
+                    total += sd * sd * sd;
+                }
+                imgs.push_back(im);
             }
-            imgs.push_back(im);
-        }
+        };
+        make(true);
+        if (total > d.max_voxels) make(false);
         unsigned char *buf = nullptr;
         long long *out = nullptr;
         Choice c;
@@ -222,29 +237,35 @@ void ecc_plan_s::autotune()
             cudaMalloc(&out, sizeof(long long) * nbins * imgs.size()) == cudaSuccess) {
             synth_fill<<<1024, 256, 0, s>>>(buf, total, es, 97, 89, d.lo, d.hi);
             for (size_t i = 0; i < imgs.size(); ++i) imgs[i].data = buf + offs[i] * es;
-            float best = 1e30f;
             // candidates: on the 4352-image uneven batch (2D sides 64-1024,
             // 3D sides 32-256) 2D chunks of 64 rows ran 8 % slower than 16
             // or 32, and 3D chunks of 8 or 32 planes 3-5 % slower than 16
             // or 24 (short chunks re-read more halo planes, long ones leave
-            // warps idle at the end of the work list)
-            for (int c2 : {16, 32})
-                for (int c3 : {16, 24}) {
+            // warps idle at the end of the work list).  These lengths serve
+            // batches below the work-list kernel's large-batch threshold
+            // (which take 32 x 24), so the mix is of that size.  Three
+            // interleaved rounds, each candidate's best; the first is kept
+            // unless another is at least 3 % faster.
+            const int cand[4][2] = {{32, 24}, {32, 16}, {16, 24}, {16, 16}};
+            float best_of[4] = {1e30f, 1e30f, 1e30f, 1e30f};
+            for (int round = 0; round < 3; ++round)
+                for (int ci = 0; ci < 4; ++ci) {
                     release_batch(this);
-                    tuned_batch[0] = c2;
-                    tuned_batch[1] = c3;
+                    tuned_batch[0] = cand[ci][0];
+                    tuned_batch[1] = cand[ci][1];
                     const float ms = time_ms(
                         [&] {
                             ecc_compute_batch(this, (int32_t)imgs.size(), imgs.data(), reinterpret_cast<int64_t *>(out),
                                               s);
                         },
                         s, 3);
-                    if (ms < best) {
-                        best = ms;
-                        c.a = c2;
-                        c.b = c3;
-                    }
+                    best_of[ci] = ms < best_of[ci] ? ms : best_of[ci];
                 }
+            int pick = 0;
+            for (int ci = 1; ci < 4; ++ci)
+                if (best_of[ci] < 0.97f * best_of[0] && best_of[ci] < best_of[pick]) pick = ci;
+            c.a = cand[pick][0];
+            c.b = cand[pick][1];
             release_batch(this);
             cudaStreamSynchronize(s);
         }
