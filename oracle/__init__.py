@@ -206,9 +206,10 @@ def ecc_levels(img: np.ndarray, levels, mode: str = VERTEX, threads: int = 1) ->
 def present_levels(img: np.ndarray) -> np.ndarray:
     """Eq. 1's thresholds of a float32 image: the values present in it,
     distinct and ascending (t_1 < t_2 < ... < t_n, Sec. 2.2).  NaN voxels
-    define no threshold (they count as +infinity, above every level), and
-    -0.0 is the value 0.0 (it compares equal to it, so it is the same
-    threshold), returned as +0.0.  A library sort-unique is the step."""
+    define no threshold and lie in no sublevel set (v <= t is false for
+    every t, +infinity included), and -0.0 is the value 0.0 (it compares
+    equal to it, so it is the same threshold), returned as +0.0.  A library
+    sort-unique is the step."""
     v = np.asarray(img, dtype=np.float32).ravel()
     v = v[~np.isnan(v)]
     return np.unique(v + np.float32(0.0)).astype(np.float32)

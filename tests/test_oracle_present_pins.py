@@ -86,13 +86,99 @@ def test_last_level_is_the_full_box_without_nan(mode):
         assert e[-1] == 1
 
 
-def test_planted_mistakes_are_caught():
-    img = np.array([[np.nan, -0.0, 0.0], [1.0, 1.0, -2.0]], np.float32)
-    want = _distinct_by_equality(img)
-    # NaN kept as a threshold, -0.0 kept apart from 0.0, or the values unsorted
-    keep_nan = np.unique(img.ravel())
-    assert keep_nan.size != len(want)
-    keep_negzero_bits = np.unique(img.ravel()[~np.isnan(img.ravel())].view(np.uint32)).view(np.float32)
-    assert keep_negzero_bits.size != len(want)
-    unsorted = np.array(list(dict.fromkeys(img.ravel()[~np.isnan(img.ravel())].tolist())), np.float32)
-    assert unsorted.tolist() != want
+# ---------------------------------------------------------------- mutants
+# Each one is a plausible mistake in present_levels or ecc_present; the pins
+# above, run on the mutant instead of the oracle, must fail.
+
+def _finite(img):
+    v = np.asarray(img, np.float32).ravel()
+    return v[~np.isnan(v)]
+
+
+def _levels_keep_nan(img):
+    return np.unique(np.asarray(img, np.float32).ravel() + np.float32(0.0))
+
+
+def _levels_negzero_apart(img):
+    return np.unique(_finite(img).view(np.uint32)).view(np.float32)
+
+
+def _levels_negzero_kept(img):
+    return np.unique(_finite(img))  # a zero threshold may come out as -0.0
+
+
+def _levels_first_seen_order(img):
+    return np.array(list(dict.fromkeys(_finite(img).tolist())), np.float32)
+
+
+def _levels_descending(img):
+    return oracle.present_levels(img)[::-1].copy()
+
+
+def _present_with(levels_fn):
+    def fn(img, mode=oracle.VERTEX, threads=1):
+        lv = levels_fn(img)
+        if lv.size == 0:
+            return lv, np.zeros(0, np.int64)
+        return lv, oracle.ecc_levels(img, lv, mode, threads)
+    return fn
+
+
+def _present_nan_at_infinity(img, mode=oracle.VERTEX, threads=1):
+    lv = oracle.present_levels(img)
+    if lv.size == 0:
+        return lv, np.zeros(0, np.int64)
+    filled = np.where(np.isnan(img), np.float32(np.inf), img).astype(np.float32)
+    return lv, oracle.ecc_levels(filled, lv, mode, threads)
+
+
+def _present_strict_sublevel(img, mode=oracle.VERTEX, threads=1):
+    lv = oracle.present_levels(img)
+    if lv.size == 0:
+        return lv, np.zeros(0, np.int64)
+    below = np.nextafter(lv, np.float32(-np.inf)).astype(np.float32)  # v < t instead of v <= t
+    return lv, oracle.ecc_levels(img, below, mode, threads)
+
+
+def _present_shifted_one_level(img, mode=oracle.VERTEX, threads=1):
+    lv, e = oracle.ecc_present(img, mode, threads)
+    return lv, np.concatenate([np.zeros(min(1, e.size), np.int64), e[:-1]])
+
+
+def _pins_hold(levels_fn, present_fn) -> bool:
+    rng = np.random.default_rng(45)
+    for _ in range(60):
+        shape = tuple(int(x) for x in rng.integers(1, 6, size=int(rng.integers(2, 4))))
+        img = _rand_img(rng, shape)
+        got = np.asarray(levels_fn(img))
+        want = _distinct_by_equality(img)
+        if got.dtype != np.float32 or got.tolist() != want:
+            return False
+        if np.any(np.signbit(got[got == 0])):
+            return False
+        for mode in MODES:
+            lv, e = present_fn(img, mode)
+            if not np.array_equal(np.asarray(lv).view(np.uint32), got.view(np.uint32)):
+                return False
+            if not np.array_equal(e, pins.bruteforce_ecc_levels(img, got.astype(np.float64), mode)):
+                return False
+    return True
+
+
+def test_pins_hold_for_the_oracle():
+    assert _pins_hold(oracle.present_levels, oracle.ecc_present)
+
+
+LEVEL_MUTANTS = [_levels_keep_nan, _levels_negzero_apart, _levels_negzero_kept, _levels_first_seen_order,
+                 _levels_descending]
+PRESENT_MUTANTS = [_present_nan_at_infinity, _present_strict_sublevel, _present_shifted_one_level]
+
+
+@pytest.mark.parametrize("mutant", LEVEL_MUTANTS, ids=[m.__name__ for m in LEVEL_MUTANTS])
+def test_planted_level_mistakes_are_caught(mutant):
+    assert not _pins_hold(mutant, _present_with(mutant))
+
+
+@pytest.mark.parametrize("mutant", PRESENT_MUTANTS, ids=[m.__name__ for m in PRESENT_MUTANTS])
+def test_planted_ecc_mistakes_are_caught(mutant):
+    assert not _pins_hold(oracle.present_levels, mutant)
