@@ -890,7 +890,7 @@ def run_serving(args):
                            "first": [(i, list(views[i][0].shape), str(views[i][0].dtype)) for i in (mism_rt + mism_sat)[:4]]}}
 
 
-def main():
+def arg_parser() -> argparse.ArgumentParser:
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=None,
                     help="GPUs (one rank each); default: WORLD_SIZE under a launcher, else 1")
@@ -922,7 +922,11 @@ def main():
     ap.add_argument("--only-c4", default=None, choices=["all", "2d", "3d"],
                     help="profiler runs: only the uneven batch, or its 2D or 3D images (three calls after "
                          "the checked one)")
-    args = ap.parse_args()
+    return ap
+
+
+def main():
+    args = arg_parser().parse_args()
     args.warmup = max(args.warmup, 3)
     ws_env = int(os.environ.get("WORLD_SIZE", "1"))
     if args.gpus is None:
