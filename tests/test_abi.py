@@ -75,6 +75,9 @@ def test_null_plan_is_rejected_by_every_plan_entry_point(lib):
         "ecc_compute_nd": lambda: lib.ecc_compute_nd(None, None, None, None, None),
         "ecc_pipeline_gaussian": lambda: lib.ecc_pipeline_gaussian(None, None, None, 13, 1, None, 1, None, None),
         "ecc_status_get": lambda: lib.ecc_status_get(None, None),
+        "ecc_levels_present": lambda: lib.ecc_levels_present(None, None, None, 1, None, None),
+        "ecc_compute_present": lambda: lib.ecc_compute_present(None, None, None, 1, None, None, None),
+        "ecc_server_prepare": lambda: lib.ecc_server_prepare(None, ecc.ECC_U8, 0, 255, ecc.ECC_VERTEX_MAX),
     }
     for name, call in calls.items():
         assert call() == inval, name
@@ -82,3 +85,14 @@ def test_null_plan_is_rejected_by_every_plan_entry_point(lib):
     ms, n = ctypes.c_double(), ctypes.c_int64()
     assert lib.ecc_plan_kernel_time(None, ctypes.byref(ms), ctypes.byref(n)) == inval
     assert lib.ecc_plan_last_launches(None) == -1
+
+
+def test_a_missing_library_is_an_error_not_a_fallback(monkeypatch, tmp_path):
+    """Without the built CUDA library every call raises: there is no CPU path."""
+    from paper_2203_09087_gb300 import _binding
+    monkeypatch.setattr(_binding, "_lib", None)
+    monkeypatch.setattr(_binding, "library_path", lambda: tmp_path / "libecc_gb300.so")
+    with pytest.raises(RuntimeError, match="missing"):
+        _binding.library()
+    with pytest.raises(RuntimeError, match="missing"):
+        ecc.ecc_last_error()
